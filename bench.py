@@ -1,0 +1,344 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the cutoff non-bonded MD path on GB300.
+
+One step = one velocity-Verlet MD step of the 92,224-atom ApoA1-box lattice through
+the C ABI (md_step: kick, drift + wrap, cell rebuild, forces, kick).  The headline
+metric is within-cutoff pair interactions per second (unique pairs with r^2 < rc^2
+per step, divided by the device time per step); ms_per_step gives MD steps/s.
+
+Prints ONE JSON line (rank 0).  Multi-GPU runs (torchrun) are independent replicas
+(the path has no exchange step): every rank runs the same system, value = all ranks'
+pairs / max-over-ranks time, scaling "weak".
+
+--impl reference times the FP64 CPU oracle on the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "within-cutoff pair interactions/sec"
+UNIT = "pairs/s"
+L2_FLUSH_BYTES = 256 << 20  # twice the 129 MB L2
+FP32_LANES_PER_SM = 128
+NUM_SMS = 152
+# algorithmic FLOPs (FMA = 2): per half-shell candidate pair (3 sub, 3 mul, 2 add) and
+# per surviving pair (powers, Eq. 1-2 factor, F = f r, reaction)
+FLOP_PER_CANDIDATE = 8
+FLOP_PER_PAIR = 22
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=92224, help="atoms (lattice at ApoA1 density)")
+    ap.add_argument("--mode", default="f32", choices=["f32", "fixed64"])
+    ap.add_argument("--algo", type=int, default=0)
+    ap.add_argument("--dt", type=float, default=1.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload(n):
+    from paper_1611_04474_gb300 import workloads as W
+
+    base = W.workload_lattice_92k() if n == W.APOA1_N else W.lattice_box(n=n, seed=2)
+    # sigma halved and masses 12-16 amu: the same atoms, charges, box and cutoff (so the
+    # same cell list and pair count), but a force field under which the dynamics stays
+    # physical for the timed steps
+    return base.with_forcefield(sigma_scale=0.5, mass_range=(12.0, 16.0), seed=22)
+
+
+def half_shell_candidates(cell_start: np.ndarray, dims) -> int:
+    """Candidate pairs of one force evaluation under the half-shell cell-pair scheme:
+    n_c (n_c - 1)/2 per home cell plus n_c n_c' over its 13 forward neighbours."""
+    nx, ny, nz = dims
+    cnt = np.diff(cell_start.astype(np.int64)).reshape(nz, ny, nx)
+    total = int((cnt * (cnt - 1) // 2).sum())
+    offs = [(1, 0, 0), (-1, 1, 0), (0, 1, 0), (1, 1, 0)]
+    offs += [(ox, oy, 1) for oy in (-1, 0, 1) for ox in (-1, 0, 1)]
+    seen = set()
+    for ox, oy, oz in offs:
+        key = (ox % nx, oy % ny, oz % nz)
+        if key in seen or key == (0, 0, 0):
+            continue
+        seen.add(key)
+        other = np.roll(cnt, shift=(-oz, -oy, -ox), axis=(0, 1, 2))
+        total += int((cnt * other).sum())
+    return total
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_rate(s, seconds: float, seed: int = 0):
+    """The FP64 oracle as it stands, single-threaded, on a sample of the workload's atoms:
+    forces on sampled atoms over the full cell list.  Returns (pairs/s, sample text)."""
+    import oracle
+
+    ff = oracle.ForceField.from_system(s)
+    p = s.pos.astype(np.float64)
+    rng = np.random.default_rng(seed)
+    sample = 2048
+    done_pairs = 0.0
+    t_total = 0.0
+    rounds = 0
+    while t_total < seconds:
+        sel = rng.choice(s.n, size=sample, replace=False).astype(np.int32)
+        t0 = time.perf_counter()
+        _, _, npart = oracle.forces_atoms(p, s.q, s.type, s.box, ff, sel)
+        t_total += time.perf_counter() - t0
+        done_pairs += float(npart.sum()) / 2.0  # each unique pair is met from both sides
+        rounds += 1
+    return done_pairs / t_total, (f"oracle full-shell cell-list forces on {rounds} random samples of "
+                                  f"{sample} of the {s.n} atoms ({t_total:.1f} s); unique-pair "
+                                  f"equivalent = partner count / 2")
+
+
+def run_reference(args):
+    world, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    s = workload(args.n)
+    per_step_s = 2.0
+    rates = []
+    for k in range(args.warmup + args.steps):
+        r, sample = cpu_oracle_rate(s, per_step_s, seed=k)
+        if k >= args.warmup:
+            rates.append(r)
+    value = statistics.mean(rates)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"lattice_{s.n}_apoa1_box", "atoms": s.n, "rc": s.rc,
+                       "box": [float(x) for x in s.box]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_1611_04474_gb300 import api
+
+    api.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    mode = api.ACCUM_F32 if args.mode == "f32" else api.ACCUM_FIXED64
+    s = workload(args.n)
+    eng = api.Engine(s, mode=mode, algo=args.algo, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    # pair count and candidate count of the starting state (counter run, untimed)
+    eng.build_cells()
+    eng.compute_forces(count=True)
+    torch.cuda.synchronize()
+    pairs_start = int(eng.pair_count.item())
+    candidates = half_shell_candidates(eng.cells.cell_start.cpu().numpy(), eng.dims)
+
+    # warm-up MD steps
+    for _ in range(args.warmup):
+        eng.step(1, dt_fs=args.dt)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(dev.index)
+    if world > 1:
+        torch.distributed.barrier()
+    clocks.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        ev[k][0].record(stream)
+        eng.step(1, dt_fs=args.dt)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+
+    # the dominant kernel alone on the final state: forces after a rebuilt cell list
+    eng.pos_q[:, :3] = eng.pos.to(torch.float32)
+    eng.build_cells()
+    fev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        fev[k][0].record(stream)
+        eng.compute_forces()
+        fev[k][1].record(stream)
+    torch.cuda.synchronize()
+    force_ms = [a.elapsed_time(b) for a, b in fev]
+    eng.compute_forces(count=True)
+    torch.cuda.synchronize()
+    pairs_end = int(eng.pair_count.item())
+    status = int(eng.status.item())
+    clk = clocks.stop()
+
+    # end to end through the public API with host buffers: pinned state in, result out
+    pos_h = eng.pos.cpu().pin_memory()
+    vel_h = eng.vel.cpu().pin_memory()
+    F_h = eng.forces.cpu().pin_memory()
+    en_h = torch.empty((1, 4), dtype=torch.float64).pin_memory()
+    elog = torch.empty((1, 4), dtype=torch.float64, device=dev)
+    h2d = pos_h.numel() * 8 + vel_h.numel() * 8 + F_h.numel() * F_h.element_size()
+    d2h = h2d + en_h.numel() * 8
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        e2e_ev[k][0].record(stream)
+        eng.pos.copy_(pos_h, non_blocking=True)
+        eng.vel.copy_(vel_h, non_blocking=True)
+        eng.forces.copy_(F_h, non_blocking=True)
+        eng.step(1, dt_fs=args.dt, energy_log=elog)
+        pos_h.copy_(eng.pos, non_blocking=True)
+        vel_h.copy_(eng.vel, non_blocking=True)
+        F_h.copy_(eng.forces, non_blocking=True)
+        en_h.copy_(elog, non_blocking=True)
+        e2e_ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = [a.elapsed_time(b) for a, b in e2e_ev]
+
+    t_step = sum(step_ms)
+    t_force = statistics.mean(force_ms)
+    t_e2e = sum(e2e_ms)
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([t_step, t_e2e], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_step, t_e2e = float(t[0]), float(t[1])
+    pairs_per_step = 0.5 * (pairs_start + pairs_end)
+    total_pairs = pairs_per_step * args.steps * world
+    value = total_pairs / (t_step / 1e3)
+    e2e_value = total_pairs / (t_e2e / 1e3)
+
+    flops = FLOP_PER_CANDIDATE * candidates + FLOP_PER_PAIR * pairs_end
+    sm_clock_ghz = 2.07
+    peak_tflops = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_clock_ghz / 1e3
+    achieved = flops / (t_force / 1e3) / 1e12
+    per_step_launches = 8  # kick, drift+wrap, 4 cell-build kernels, forces, kick
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if mode == api.ACCUM_F32 else "f32+int64",
+        "data": "synthetic",
+        "config": {"workload": f"lattice_{s.n}_apoa1_box", "atoms": s.n, "box": [float(x) for x in s.box],
+                   "rc": s.rc, "cells": eng.dims, "step": "velocity-Verlet MD step (rebuild+forces+VV)",
+                   "force_field": "8 LJ types, sigma x0.5 (1.25-1.9 A), masses 12-16 amu, q~N(0,0.4)",
+                   "accum": args.mode, "algo": args.algo, "dt_fs": args.dt,
+                   "l2": "flushed (256 MB write) before every timed step",
+                   "parallelism": f"replicas x{world}"},
+        "md_steps_per_s": 1e3 * args.steps / t_step,
+        "pairs_per_step": pairs_per_step,
+        "candidates_per_eval": candidates,
+        "force_kernel_ms": t_force,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved / peak_tflops, "traffic": None,
+                     "kernel": "md_nonbonded_forces",
+                     "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz (derived)"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": args.steps * per_step_launches + args.steps,
+        "clocks": clk,
+        "status": status,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, sample = cpu_oracle_rate(s, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": sample}
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,182 @@
+/*
+ * md_nonbonded.h -- C ABI of the GB300 cutoff non-bonded molecular-dynamics force path.
+ *
+ * The library evaluates the short-range non-bonded forces of the paper
+ * (Section II.A): Lennard-Jones, Eq. 1  F = (A/|r|^14 - B/|r|^8) * r, plus
+ * Coulomb, Eq. 2  F = k*q1*q2/|r|^3 * r, for every pair of atoms closer than
+ * the cutoff radius rc (strictly: r^2 < rc^2), found through a periodic cell
+ * list whose cells have edge >= rc, so that each home cell meets only its
+ * 3x3x3 neighbour cells (Section II.A, Fig. 2, Algorithm 1).  Beyond rc the
+ * force is zero; long-range electrostatics is outside this library (the paper
+ * leaves it to the host).  A velocity-Verlet integrator wraps the force call.
+ *
+ * Conventions shared by every entry point
+ *   - Units: Angstrom, fs, amu, elementary charge, kcal/mol.
+ *   - r = x_i - x_j under the minimum-image convention; the force above acts
+ *     on atom i and its reaction -F on atom j.
+ *   - All array arguments are DEVICE pointers owned by the caller unless the
+ *     comment says "host".  The library never allocates, frees or keeps caller
+ *     memory; scratch lives in the caller's `workspace` (size from
+ *     md_workspace_bytes).  Every call is asynchronous on `stream` (a
+ *     cudaStream_t passed as void*; NULL is the legacy default stream) and
+ *     returns after enqueuing its kernels.
+ *   - Return value: MD_OK (0) or a negative MD_ERR_* code from host-side
+ *     validation or a failed launch; nothing is enqueued when validation fails.
+ *   - Conditions found on the device are OR-ed into *status (a device uint32
+ *     the caller zeroes and reads after synchronising; may be NULL) as
+ *     MD_STATUS_* bits.  Kernels never trap.
+ *   - Box: host double[3] edge lengths of an orthorhombic periodic box.  The
+ *     cutoff must satisfy 0 < rc < min(L)/2 (else MD_ERR_CUTOFF).
+ *   - Cells: dims[d] = max(1, floor(L_d / rc)) per axis (md_cell_dims); a
+ *     coordinate x is wrapped in FP64 as w = x - L*floor(x/L) folded into
+ *     [0, L), its cell index along the axis is floor(w * (dims/L)) clamped to
+ *     [0, dims-1], the flat cell index is cx + dims0*(cy + dims1*cz), and the
+ *     atoms of a cell are kept in ascending input order.
+ */
+#ifndef MD_NONBONDED_H
+#define MD_NONBONDED_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MD_ABI_VERSION 1
+
+/* return codes */
+#define MD_OK 0
+#define MD_ERR_INVALID_ARG (-1) /* n < 0, NULL where required, ntypes outside 1..32, dt <= 0 ... */
+#define MD_ERR_CUTOFF (-2)      /* rc <= 0, rc >= min(L)/2, or dims disagree with md_cell_dims */
+#define MD_ERR_WORKSPACE (-3)   /* workspace NULL or smaller than md_workspace_bytes */
+#define MD_ERR_CUDA (-4)        /* a kernel launch or async CUDA call failed */
+#define MD_ERR_TOO_LARGE (-5)   /* more cells or atoms than the index types hold */
+
+/* device status bits */
+#define MD_STATUS_NONFINITE 1u      /* a non-finite position or force was seen */
+#define MD_STATUS_FIXED_OVERFLOW 2u /* a pair term reached 2^31 kcal/mol/A in MD_ACCUM_FIXED64 */
+#define MD_STATUS_BAD_TYPE 4u       /* an LJ type outside [0, ntypes) was read as type 0 */
+
+/* accumulation / precision modes (argument `mode`) */
+#define MD_ACCUM_F32 0     /* FP32 pair math and FP32 accumulation; forces float[n][3] */
+#define MD_ACCUM_FIXED64 1 /* FP32 pair math; every pair term rounded (to nearest even) to a
+                              two's-complement int64 at scale 2^32 and summed exactly, so the
+                              result is independent of summation order and bit-reproducible;
+                              forces int64[n][3] (divide by 2^32 for kcal/mol/A) */
+#define MD_ACCUM_F64 2     /* FP64 pair math and accumulation, a slow reference mode;
+                              forces double[n][3] */
+
+/* force-kernel choice for md_nonbonded_forces_algo (md_nonbonded_forces picks the default) */
+#define MD_ALGO_DEFAULT 0
+#define MD_ALGO_FULL_SHELL 1 /* one thread per home atom over all 27 neighbour cells (Alg. 1) */
+#define MD_ALGO_HALF_SHELL 2 /* each cell pair once, reactions by Newton's third law */
+
+/* Force-field constants of Eq. 1-2.  Host struct; AB is a DEVICE pointer to
+ * float[ntypes][ntypes][2] holding (A_ij, B_ij) of Eq. 1 (symmetric in i,j). */
+typedef struct md_forcefield {
+    int32_t ntypes;   /* 1..32 */
+    int32_t reserved; /* set to 0 */
+    const float *AB;
+    double k_coulomb; /* k of Eq. 2, kcal*A/(mol*e^2), e.g. 332.0636 */
+    double rc;        /* cutoff radius, A */
+} md_forcefield;
+
+/* Human-readable text for a return code (static storage, never NULL). */
+const char *md_strerror(int code);
+
+/* MD_ABI_VERSION of the loaded library. */
+int md_abi_version(void);
+
+/* Cells per axis for a box and cutoff (Section II.A: cell edge roughly equal to rc,
+ * here edge >= rc).  Host only: box_L host double[3], dims_out host int32[3].
+ * MD_ERR_CUTOFF when rc <= 0 or rc >= min(L)/2. */
+int md_cell_dims(const double *box_L, double rc, int32_t *dims_out);
+
+/* Bytes of scratch every entry point below needs for n atoms and these cell dims
+ * (host int32[3]); 0 on invalid arguments.  One workspace of this size serves
+ * any entry point, but concurrent calls must not share one. */
+size_t md_workspace_bytes(int32_t n, const int32_t *dims);
+
+/*
+ * md_build_cells -- bin atoms into cells by a counting sort (Section II.A cell list;
+ * Section II.B item 2: per-cell arrays instead of linked lists).
+ *   pos_q         [n][4] float: x, y, z, q in input order (any real coordinates;
+ *                 they are wrapped into the box)
+ *   type          [n] int32 LJ type
+ *   dims          host int32[3] from md_cell_dims(box_L, rc)
+ * Outputs (device, caller-allocated):
+ *   cell_start    [ncell+1] int32: atoms of cell c are sorted slots
+ *                 cell_start[c] .. cell_start[c+1]-1, ncell = dims0*dims1*dims2
+ *   perm          [n] int32: sorted slot -> input index
+ *   pos_q_sorted  [n][4] float: wrapped x, y, z (rounded to float from the FP64
+ *                 wrap) and q, in sorted order
+ *   type_sorted   [n] int32, in sorted order
+ * A non-finite coordinate sets MD_STATUS_NONFINITE and the atom goes to cell 0 at
+ * the origin.  The result is deterministic (stable order within a cell).
+ */
+int md_build_cells(const float *pos_q, const int32_t *type, int32_t n, const double *box_L,
+                   const int32_t *dims, int32_t *cell_start, int32_t *perm, float *pos_q_sorted,
+                   int32_t *type_sorted, void *workspace, size_t ws_bytes, uint32_t *status,
+                   void *stream);
+
+/*
+ * md_nonbonded_forces -- short-range non-bonded forces (Eq. 1 + Eq. 2 with the cutoff of
+ * Section II.A) over the cell list that md_build_cells produced, in the order of
+ * Algorithm 1: each home cell meets its neighbour cells, each candidate pair passes
+ * the filter r^2 < rc^2, and only the surviving pairs reach the force computation.
+ *   cell_start, perm, pos_q_sorted, type_sorted   as returned by md_build_cells
+ *   ff            host pointer to the force field (AB on the device)
+ *   mode          MD_ACCUM_F32 / MD_ACCUM_FIXED64 / MD_ACCUM_F64
+ *   forces_out    [n][3] in INPUT atom order; element type by mode (float, int64,
+ *                 double); fully overwritten (the callee zeroes it)
+ *   energy_virial_out  device double[3] = {E_LJ, E_Coulomb, W} or NULL, with
+ *                 U_LJ = A/(12 r^12) - B/(6 r^6), U_C = k q1 q2 / r, W = sum f r^2
+ *                 (F = f r); summed per block and then in a fixed order
+ *   pair_count_out     device uint64[1] or NULL: unique pairs with r^2 < rc^2
+ * Forces and counts of modes FIXED64 and F64 are reproducible bit for bit; F32 uses
+ * floating-point atomics in the half-shell kernel and may differ in the last bits
+ * between runs.
+ */
+int md_nonbonded_forces(const int32_t *cell_start, const int32_t *perm, const float *pos_q_sorted,
+                        const int32_t *type_sorted, int32_t n, const double *box_L,
+                        const int32_t *dims, const md_forcefield *ff, int32_t mode,
+                        void *forces_out, double *energy_virial_out,
+                        unsigned long long *pair_count_out, void *workspace, size_t ws_bytes,
+                        uint32_t *status, void *stream);
+
+/* The same with an explicit force kernel (MD_ALGO_*).  Every algorithm computes the
+ * same forces up to floating-point rounding (bit for bit in FIXED64 and F64). */
+int md_nonbonded_forces_algo(const int32_t *cell_start, const int32_t *perm,
+                             const float *pos_q_sorted, const int32_t *type_sorted, int32_t n,
+                             const double *box_L, const int32_t *dims, const md_forcefield *ff,
+                             int32_t mode, int32_t algo, void *forces_out,
+                             double *energy_virial_out, unsigned long long *pair_count_out,
+                             void *workspace, size_t ws_bytes, uint32_t *status, void *stream);
+
+/*
+ * md_step -- n_steps of kick-drift-kick velocity Verlet around the force call (the
+ * paper's iteration: forces, then the motion update; Sections I and II.A).  Per step:
+ *   v += dt/2 * a;  x += dt * v;  x <- wrap(x);  rebuild cells;  F = F(x);  v += dt/2 * a
+ * with a = F * inv_mass * 4.184e-4 (A/fs^2 per (kcal/mol/A)/amu).  Positions and
+ * velocities are FP64 state; the force call sees the positions rounded to float.
+ *   pos           [n][3] double in/out, A (wrapped into the box on exit)
+ *   vel           [n][3] double in/out, A/fs
+ *   forces        [n][3] in/out in the mode's element type: on entry F(pos) when
+ *                 forces_valid != 0 (else it is computed first), on exit F(pos_out)
+ *   inv_mass      [n] float, 1/amu;  q [n] float;  type [n] int32
+ *   energy_log    device double[n_steps][4] = {E_LJ, E_Coulomb, KE, W} after each
+ *                 step, or NULL (then no energies are computed)
+ * The cells are rebuilt every step (no Verlet skin).  Status bits as above.
+ */
+int md_step(double *pos, double *vel, void *forces, int32_t forces_valid, const float *inv_mass,
+            const float *q, const int32_t *type, int32_t n, const double *box_L,
+            const md_forcefield *ff, int32_t mode, double dt_fs, int32_t n_steps,
+            double *energy_log, void *workspace, size_t ws_bytes, uint32_t *status,
+            void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MD_NONBONDED_H */

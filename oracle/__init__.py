@@ -49,7 +49,7 @@ def _load():
             lib.orc_cell_dims.argtypes = [P, f64, P]
             lib.orc_build_cells.argtypes = [i32, P, P, P, P, P, P]
             lib.orc_pair.argtypes = [P, P, P, f64, f64, f64, f64, f64, f64, P, P]
-            lib.orc_forces_cells.argtypes = [i32, P, P, P, P, i32, P, P, f64, f64, P, P, P, P, P]
+            lib.orc_forces_cells.argtypes = [i32, P, P, P, P, i32, P, P, f64, f64, P, P, P, P, P, P]
             lib.orc_forces_atoms.argtypes = [i32, P, P, P, P, i32, P, P, f64, f64, i32, P, P, P, P]
             lib.orc_forces_brute.argtypes = [i32, P, P, P, P, i32, P, P, f64, f64, P, P, P]
             lib.orc_boundary_pairs.argtypes = [i32, P, P, f64, f64, i32, P, P]
@@ -132,9 +132,10 @@ def pair(xi, xj, box, qi, qj, A, B, k, rc):
 
 
 class Result:
-    def __init__(self, F, energy, npairs, cond=None, fabs_sum=None):
+    def __init__(self, F, energy, npairs, cond=None, fabs_sum=None, energy_abs=None):
         self.F = F  # float64 [N, 3]
         self.energy = energy  # float64 [3]: E_LJ, E_C, W
+        self.energy_abs = energy_abs  # float64 [3]: the same sums over absolute term sizes
         self.npairs = npairs  # unique pairs within the cutoff
         self.cond = cond  # float64 [N]
         self.fabs_sum = fabs_sum  # float64 [N]
@@ -150,13 +151,15 @@ def forces_cells(pos, q, types, box, ff: ForceField, with_cond: bool = True) -> 
     cond = np.zeros(n) if with_cond else None
     fabs_sum = np.zeros(n) if with_cond else None
     npairs = ctypes.c_longlong(0)
+    eabs = np.zeros(3)
     rcode = lib.orc_forces_cells(n, _p(pos), _p(_f64(q)), _p(_i32(types)), _p(_f64(box)),
                                  ff.ntypes, _p(ff.A), _p(ff.B), ff.k, ff.rc, _p(F), _p(en),
                                  _p(cond) if with_cond else None,
-                                 _p(fabs_sum) if with_cond else None, ctypes.byref(npairs))
+                                 _p(fabs_sum) if with_cond else None, ctypes.byref(npairs),
+                                 _p(eabs))
     if rcode:
         raise RuntimeError(f"orc_forces_cells failed ({rcode})")
-    return Result(F, en, int(npairs.value), cond, fabs_sum)
+    return Result(F, en, int(npairs.value), cond, fabs_sum, eabs)
 
 
 def forces_atoms(pos, q, types, box, ff: ForceField, sel):

@@ -197,18 +197,20 @@ static int cl_make(cell_list *cl, int n, const double *pos, const double *L, dou
  * Every pair is met twice (once from each side), so energies and the virial
  * take half of each meeting.  Outputs (any may be NULL except F):
  *   F[n*3], energy[3] = {E_LJ, E_C, W}, cond[n] = sum over partners of the
- *   term sizes, fabs_sum[n] = sum over partners of |F_ij|, npairs = unique pairs.
+ *   term sizes, fabs_sum[n] = sum over partners of |F_ij|, npairs = unique pairs,
+ *   energy_abs[3] = the same sums as energy[] taken over absolute term sizes.
  */
 int orc_forces_cells(int n, const double *pos, const double *q, const int *type,
                      const double *L, int ntypes, const double *A, const double *B,
                      double k, double rc, double *F, double *energy, double *cond,
-                     double *fabs_sum, long long *npairs)
+                     double *fabs_sum, long long *npairs, double *energy_abs)
 {
     cell_list cl;
     int rcode = cl_make(&cl, n, pos, L, rc);
     if (rcode) return rcode;
     double rc2 = rc * rc;
     double e_lj = 0.0, e_cl = 0.0, vir = 0.0;
+    double a_lj = 0.0, a_cl = 0.0, a_vir = 0.0;
     long long ordered = 0;
     for (int i = 0; i < 3 * n; ++i) F[i] = 0.0;
     if (cond) for (int i = 0; i < n; ++i) cond[i] = 0.0;
@@ -237,6 +239,9 @@ int orc_forces_cells(int n, const double *pos, const double *q, const int *type,
                     e_lj += 0.5 * t.u_lj;
                     e_cl += 0.5 * t.u_cl;
                     vir += 0.5 * t.f * r2;
+                    a_lj += 0.5 * (fabs(A[tp]) / 12.0 * pow(r2, -6.0) + fabs(B[tp]) / 6.0 * pow(r2, -3.0));
+                    a_cl += 0.5 * fabs(t.u_cl);
+                    a_vir += 0.5 * t.cond * sqrt(r2);
                     if (cond) cond[i] += t.cond;
                     if (fabs_sum) fabs_sum[i] += fabs(t.f) * sqrt(r2);
                     ordered++;
@@ -246,6 +251,7 @@ int orc_forces_cells(int n, const double *pos, const double *q, const int *type,
         }
     }
     if (energy) { energy[0] = e_lj; energy[1] = e_cl; energy[2] = vir; }
+    if (energy_abs) { energy_abs[0] = a_lj; energy_abs[1] = a_cl; energy_abs[2] = a_vir; }
     if (npairs) *npairs = ordered / 2;
     cl_free(&cl);
     return 0;
@@ -396,7 +402,7 @@ int orc_vv_steps(int n, double *pos, double *vel, double *F, int f_valid,
         for (int i_ = 0; i_ < 3 * n; ++i_)                                        \
             xf[i_] = f32_positions ? (double)(float)pos[i_] : pos[i_];            \
         rcode = orc_forces_cells(n, xf, q, type, L, ntypes, A, B, k, rc, F, en,   \
-                                 NULL, NULL, NULL);                               \
+                                 NULL, NULL, NULL, NULL);                         \
     } while (0)
     if (!f_valid) ORC_FORCES();
     for (int s = 0; s < n_steps && rcode == 0; ++s) {

@@ -1,0 +1,285 @@
+"""Thin Python binding of the C ABI in include/md_nonbonded.h (argument marshalling only).
+
+Every computation runs in the CUDA kernels of libmdnb.so; this module checks
+tensor dtypes, devices and shapes, passes raw device pointers and the current
+CUDA stream, and turns negative return codes into exceptions.  There is no CPU
+path: if the library is missing, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmdnb.so")
+
+ACCUM_F32 = 0
+ACCUM_FIXED64 = 1
+ACCUM_F64 = 2
+ALGO_DEFAULT = 0
+ALGO_FULL_SHELL = 1
+ALGO_HALF_SHELL = 2
+STATUS_NONFINITE = 1
+STATUS_FIXED_OVERFLOW = 2
+STATUS_BAD_TYPE = 4
+FIXED_SCALE = 2.0**32
+
+EXPORTS = ("md_strerror", "md_abi_version", "md_cell_dims", "md_workspace_bytes", "md_build_cells",
+           "md_nonbonded_forces", "md_nonbonded_forces_algo", "md_step")
+
+_lib = None
+
+
+class MDError(RuntimeError):
+    def __init__(self, fn: str, code: int, text: str):
+        super().__init__(f"{fn} failed: {text} ({code})")
+        self.code = code
+
+
+class md_forcefield(ctypes.Structure):
+    _fields_ = [("ntypes", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("AB", ctypes.c_void_p), ("k_coulomb", ctypes.c_double), ("rc", ctypes.c_double)]
+
+
+def load(path: str | None = None):
+    """Load libmdnb.so (built by ``__graft_entry__.build()``).  Raises if it is missing."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} is missing: build it with `python -c 'import __graft_entry__ as g; "
+                           f"g.build()'` (there is no fallback implementation)")
+    lib = ctypes.CDLL(p)
+    V, P, i32, f64, sz = None, ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_size_t
+    lib.md_strerror.argtypes = [ctypes.c_int]
+    lib.md_strerror.restype = ctypes.c_char_p
+    lib.md_abi_version.argtypes = []
+    lib.md_abi_version.restype = ctypes.c_int
+    lib.md_cell_dims.argtypes = [P, f64, P]
+    lib.md_cell_dims.restype = ctypes.c_int
+    lib.md_workspace_bytes.argtypes = [i32, P]
+    lib.md_workspace_bytes.restype = sz
+    lib.md_build_cells.argtypes = [P, P, i32, P, P, P, P, P, P, P, sz, P, P]
+    lib.md_build_cells.restype = ctypes.c_int
+    lib.md_nonbonded_forces.argtypes = [P, P, P, P, i32, P, P, P, i32, P, P, P, P, sz, P, P]
+    lib.md_nonbonded_forces.restype = ctypes.c_int
+    lib.md_nonbonded_forces_algo.argtypes = [P, P, P, P, i32, P, P, P, i32, i32, P, P, P, P, sz,
+                                             P, P]
+    lib.md_nonbonded_forces_algo.restype = ctypes.c_int
+    lib.md_step.argtypes = [P, P, P, i32, P, P, P, i32, P, P, i32, f64, i32, P, P, sz, P, P]
+    lib.md_step.restype = ctypes.c_int
+    del V
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _check(fn: str, code: int):
+    if code != 0:
+        raise MDError(fn, code, load().md_strerror(code).decode())
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _need(t, dtype, shape=None, name="tensor"):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be on a CUDA device")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _box(box):
+    return (ctypes.c_double * 3)(*[float(x) for x in box])
+
+
+def _dims(dims):
+    return (ctypes.c_int32 * 3)(*[int(x) for x in dims])
+
+
+FORCE_DTYPE = {ACCUM_F32: torch.float32, ACCUM_FIXED64: torch.int64, ACCUM_F64: torch.float64}
+
+
+class ForceField:
+    """Force-field constants on the device: AB float32 [T, T, 2], k, rc."""
+
+    def __init__(self, AB, k_coulomb: float, rc: float, device="cuda"):
+        AB = torch.as_tensor(np.asarray(AB, dtype=np.float32)).to(device).contiguous()
+        if AB.dim() != 3 or AB.shape[0] != AB.shape[1] or AB.shape[2] != 2:
+            raise ValueError("AB must be [T, T, 2]")
+        self.AB = AB
+        self.ntypes = int(AB.shape[0])
+        self.k_coulomb = float(k_coulomb)
+        self.rc = float(rc)
+        self._c = md_forcefield(self.ntypes, 0, AB.data_ptr(), self.k_coulomb, self.rc)
+
+    @classmethod
+    def from_system(cls, s, device="cuda"):
+        return cls(s.AB, s.k_coulomb, s.rc, device)
+
+    @property
+    def c(self):
+        return ctypes.byref(self._c)
+
+
+def cell_dims(box, rc):
+    d = (ctypes.c_int32 * 3)()
+    _check("md_cell_dims", load().md_cell_dims(_box(box), float(rc), d))
+    return [int(d[0]), int(d[1]), int(d[2])]
+
+
+def workspace_bytes(n: int, dims) -> int:
+    b = int(load().md_workspace_bytes(int(n), _dims(dims)))
+    if b == 0:
+        raise ValueError("invalid n or dims")
+    return b
+
+
+def make_workspace(n: int, dims, device="cuda"):
+    return torch.empty(workspace_bytes(n, dims), dtype=torch.uint8, device=device)
+
+
+@dataclass
+class CellList:
+    dims: list
+    cell_start: torch.Tensor  # int32 [ncell+1]
+    perm: torch.Tensor  # int32 [n]
+    pos_q_sorted: torch.Tensor  # float32 [n, 4]
+    type_sorted: torch.Tensor  # int32 [n]
+
+
+def alloc_cells(n: int, dims, device="cuda") -> CellList:
+    ncell = int(np.prod(dims))
+    return CellList(list(dims), torch.empty(ncell + 1, dtype=torch.int32, device=device),
+                    torch.empty(n, dtype=torch.int32, device=device),
+                    torch.empty((n, 4), dtype=torch.float32, device=device),
+                    torch.empty(n, dtype=torch.int32, device=device))
+
+
+def build_cells(pos_q, types, box, dims, workspace, out: CellList | None = None, status=None,
+                stream=None) -> CellList:
+    """md_build_cells: bin atoms into cells; returns the sorted cell list."""
+    n = int(pos_q.shape[0])
+    _need(pos_q, torch.float32, (n, 4), "pos_q")
+    _need(types, torch.int32, (n,), "types")
+    _need(workspace, torch.uint8, None, "workspace")
+    cl = out if out is not None else alloc_cells(n, dims, pos_q.device)
+    if status is not None:
+        _need(status, torch.int32, (1,), "status")
+    _check("md_build_cells", load().md_build_cells(
+        _ptr(pos_q), _ptr(types), n, _box(box), _dims(dims), _ptr(cl.cell_start), _ptr(cl.perm),
+        _ptr(cl.pos_q_sorted), _ptr(cl.type_sorted), _ptr(workspace), workspace.numel(),
+        _ptr(status), _stream(stream)))
+    return cl
+
+
+def nonbonded_forces(cl: CellList, box, ff: ForceField, workspace, mode=ACCUM_F32,
+                     algo=ALGO_DEFAULT, forces_out=None, energy_virial=None, pair_count=None,
+                     status=None, stream=None):
+    """md_nonbonded_forces(_algo): forces [n, 3] in input order (dtype by mode)."""
+    n = int(cl.perm.shape[0])
+    dev = cl.perm.device
+    F = forces_out if forces_out is not None else torch.empty((n, 3), dtype=FORCE_DTYPE[mode],
+                                                             device=dev)
+    _need(F, FORCE_DTYPE[mode], (n, 3), "forces_out")
+    if energy_virial is not None:
+        _need(energy_virial, torch.float64, (3,), "energy_virial")
+    if pair_count is not None:
+        _need(pair_count, torch.int64, (1,), "pair_count")
+    if status is not None:
+        _need(status, torch.int32, (1,), "status")
+    _need(workspace, torch.uint8, None, "workspace")
+    _check("md_nonbonded_forces_algo", load().md_nonbonded_forces_algo(
+        _ptr(cl.cell_start), _ptr(cl.perm), _ptr(cl.pos_q_sorted), _ptr(cl.type_sorted), n,
+        _box(box), _dims(cl.dims), ff.c, int(mode), int(algo), _ptr(F), _ptr(energy_virial),
+        _ptr(pair_count), _ptr(workspace), workspace.numel(), _ptr(status), _stream(stream)))
+    return F
+
+
+def step(pos, vel, forces, forces_valid: bool, inv_mass, q, types, box, ff: ForceField, mode,
+         dt_fs: float, n_steps: int, workspace, energy_log=None, status=None, stream=None):
+    """md_step: n_steps of velocity Verlet, in place on pos/vel/forces."""
+    n = int(pos.shape[0])
+    _need(pos, torch.float64, (n, 3), "pos")
+    _need(vel, torch.float64, (n, 3), "vel")
+    _need(forces, FORCE_DTYPE[mode], (n, 3), "forces")
+    _need(inv_mass, torch.float32, (n,), "inv_mass")
+    _need(q, torch.float32, (n,), "q")
+    _need(types, torch.int32, (n,), "types")
+    _need(workspace, torch.uint8, None, "workspace")
+    if energy_log is not None:
+        _need(energy_log, torch.float64, (n_steps, 4), "energy_log")
+    if status is not None:
+        _need(status, torch.int32, (1,), "status")
+    _check("md_step", load().md_step(
+        _ptr(pos), _ptr(vel), _ptr(forces), int(bool(forces_valid)), _ptr(inv_mass), _ptr(q),
+        _ptr(types), n, _box(box), ff.c, int(mode), float(dt_fs), int(n_steps), _ptr(energy_log),
+        _ptr(workspace), workspace.numel(), _ptr(status), _stream(stream)))
+
+
+def forces_to_f64(F: torch.Tensor, mode: int) -> torch.Tensor:
+    """Forces of any mode as float64 kcal/mol/A."""
+    if mode == ACCUM_FIXED64:
+        return F.to(torch.float64) / FIXED_SCALE
+    return F.to(torch.float64)
+
+
+class Engine:
+    """Device-resident state of one system: inputs, cell list, forces, MD state and
+    workspace allocated once; every call runs the CUDA path through the C ABI."""
+
+    def __init__(self, system, mode=ACCUM_F32, algo=ALGO_DEFAULT, device="cuda"):
+        s = system
+        self.system = s
+        self.n = s.n
+        self.box = [float(x) for x in s.box]
+        self.mode = mode
+        self.algo = algo
+        self.ff = ForceField.from_system(s, device)
+        self.dims = cell_dims(self.box, s.rc)
+        self.pos_q = torch.as_tensor(s.pos_q()).to(device)
+        self.types = torch.as_tensor(s.type).to(device)
+        self.q = torch.as_tensor(s.q).to(device)
+        self.inv_mass = torch.as_tensor(s.inv_mass).to(device)
+        self.pos = torch.as_tensor(s.pos.astype(np.float64)).to(device)
+        self.vel = torch.as_tensor(s.vel).to(device)
+        self.workspace = make_workspace(self.n, self.dims, device)
+        self.cells = alloc_cells(self.n, self.dims, device)
+        self.forces = torch.zeros((self.n, 3), dtype=FORCE_DTYPE[mode], device=device)
+        self.energy_virial = torch.zeros(3, dtype=torch.float64, device=device)
+        self.pair_count = torch.zeros(1, dtype=torch.int64, device=device)
+        self.status = torch.zeros(1, dtype=torch.int32, device=device)
+        self.forces_valid = False
+
+    def build_cells(self, stream=None):
+        return build_cells(self.pos_q, self.types, self.box, self.dims, self.workspace,
+                           out=self.cells, status=self.status, stream=stream)
+
+    def compute_forces(self, energy=False, count=False, algo=None, stream=None):
+        return nonbonded_forces(self.cells, self.box, self.ff, self.workspace, self.mode,
+                                self.algo if algo is None else algo, self.forces,
+                                self.energy_virial if energy else None,
+                                self.pair_count if count else None, self.status, stream)
+
+    def step(self, n_steps=1, dt_fs=1.0, energy_log=None, stream=None):
+        step(self.pos, self.vel, self.forces, self.forces_valid, self.inv_mass, self.q,
+             self.types, self.box, self.ff, self.mode, dt_fs, n_steps, self.workspace,
+             energy_log=energy_log, status=self.status, stream=stream)
+        self.forces_valid = True

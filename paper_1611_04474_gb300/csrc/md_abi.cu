@@ -1,0 +1,311 @@
+// md_abi.cu -- the extern "C" entry points declared in include/md_nonbonded.h:
+// argument validation, workspace layout, and the order of kernel launches.
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "md_internal.cuh"
+
+namespace mdnb {
+
+namespace {
+constexpr int kMaxCells = 1 << 24;
+constexpr int kMaxAtoms = (1 << 30);
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+int validate_box(const double *L)
+{
+    if (!L) return MD_ERR_INVALID_ARG;
+    for (int d = 0; d < 3; ++d)
+        if (!(L[d] > 0.0) || !isfinite(L[d])) return MD_ERR_INVALID_ARG;
+    return MD_OK;
+}
+
+int compute_dims(const double *L, double rc, int32_t *dims)
+{
+    int e = validate_box(L);
+    if (e) return e;
+    if (!(rc > 0.0) || !isfinite(rc)) return MD_ERR_CUTOFF;
+    double lmin = fmin(L[0], fmin(L[1], L[2]));
+    if (!(rc < 0.5 * lmin)) return MD_ERR_CUTOFF;
+    long long prod = 1;
+    for (int d = 0; d < 3; ++d) {
+        double nd = floor(L[d] / rc);
+        if (nd > (double)kMaxCells) return MD_ERR_TOO_LARGE;
+        dims[d] = nd < 1.0 ? 1 : (int32_t)nd;
+        prod *= dims[d];
+    }
+    if (prod > kMaxCells) return MD_ERR_TOO_LARGE;
+    return MD_OK;
+}
+
+int check_dims(const int32_t *dims, int *ncell)
+{
+    if (!dims) return MD_ERR_INVALID_ARG;
+    long long prod = 1;
+    for (int d = 0; d < 3; ++d) {
+        if (dims[d] < 1) return MD_ERR_INVALID_ARG;
+        prod *= dims[d];
+        if (prod > kMaxCells) return MD_ERR_TOO_LARGE;
+    }
+    *ncell = (int)prod;
+    return MD_OK;
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Returns the 256-byte aligned start of the caller's workspace or nullptr.
+char *ws_base(void *workspace, size_t ws_bytes, const WsLayout &ws)
+{
+    if (!workspace) return nullptr;
+    uintptr_t p = reinterpret_cast<uintptr_t>(workspace);
+    uintptr_t a = (p + kAlign - 1) & ~(uintptr_t)(kAlign - 1);
+    if (ws_bytes < (a - p) + ws.total) return nullptr;
+    return reinterpret_cast<char *>(a);
+}
+
+int cuda_code(cudaError_t e) { return e == cudaSuccess ? MD_OK : MD_ERR_CUDA; }
+
+int check_ff(const md_forcefield *ff)
+{
+    if (!ff || !ff->AB) return MD_ERR_INVALID_ARG;
+    if (ff->ntypes < 1 || ff->ntypes > kMaxTypes) return MD_ERR_INVALID_ARG;
+    if (!isfinite(ff->k_coulomb)) return MD_ERR_INVALID_ARG;
+    if (!aligned16(ff->AB) && (reinterpret_cast<uintptr_t>(ff->AB) & 7u)) return MD_ERR_INVALID_ARG;
+    return MD_OK;
+}
+}  // namespace
+
+BoxF make_box(const double *L, const int32_t *dims)
+{
+    BoxF b;
+    long long prod = 1;
+    for (int d = 0; d < 3; ++d) {
+        b.L[d] = L[d];
+        b.Lhi[d] = (float)L[d];
+        b.Llo[d] = (float)(L[d] - (double)b.Lhi[d]);
+        b.invL[d] = (float)(1.0 / L[d]);
+        b.dims[d] = dims[d];
+        prod *= dims[d];
+    }
+    b.ncell = (int)prod;
+    return b;
+}
+
+WsLayout ws_layout(int n, int ncell)
+{
+    WsLayout w;
+    size_t nn = (size_t)(n > 0 ? n : 1);
+    size_t nc = (size_t)(ncell > 0 ? ncell : 1);
+    int slots = ncell;
+    int kin = (int)((nn + 255) / 256);
+    if (slots < kin) slots = kin;
+    if (slots < 2048) slots = 2048;
+    w.nslots = slots;
+    size_t off = 0;
+    w.cell_id = off;         off = align_up(off + sizeof(int32_t) * nn);
+    w.cell_cnt = off;        off = align_up(off + sizeof(int32_t) * nc);
+    w.perm_tmp = off;        off = align_up(off + sizeof(int32_t) * nn);
+    w.accum = off;           off = align_up(off + 32 * nn);
+    w.partials = off;        off = align_up(off + sizeof(Partial) * (size_t)slots);
+    w.ev = off;              off = align_up(off + 4 * sizeof(double));
+    w.st_cell_start = off;   off = align_up(off + sizeof(int32_t) * (nc + 1));
+    w.st_perm = off;         off = align_up(off + sizeof(int32_t) * nn);
+    w.st_pos_q_sorted = off; off = align_up(off + sizeof(float4) * nn);
+    w.st_type_sorted = off;  off = align_up(off + sizeof(int32_t) * nn);
+    w.st_pos_q = off;        off = align_up(off + sizeof(float4) * nn);
+    w.total = off;
+    return w;
+}
+
+}  // namespace mdnb
+
+using namespace mdnb;
+
+extern "C" {
+
+const char *md_strerror(int code)
+{
+    switch (code) {
+    case MD_OK: return "ok";
+    case MD_ERR_INVALID_ARG: return "invalid argument";
+    case MD_ERR_CUTOFF: return "cutoff must satisfy 0 < rc < min(L)/2 and match the cell dims";
+    case MD_ERR_WORKSPACE: return "workspace missing or smaller than md_workspace_bytes";
+    case MD_ERR_CUDA: return "CUDA launch or asynchronous call failed";
+    case MD_ERR_TOO_LARGE: return "too many atoms or cells";
+    default: return "unknown error code";
+    }
+}
+
+int md_abi_version(void) { return MD_ABI_VERSION; }
+
+int md_cell_dims(const double *box_L, double rc, int32_t *dims_out)
+{
+    if (!dims_out) return MD_ERR_INVALID_ARG;
+    return compute_dims(box_L, rc, dims_out);
+}
+
+size_t md_workspace_bytes(int32_t n, const int32_t *dims)
+{
+    int ncell = 0;
+    if (n < 0 || n > kMaxAtoms || check_dims(dims, &ncell) != MD_OK) return 0;
+    return ws_layout(n, ncell).total + kAlign;
+}
+
+int md_build_cells(const float *pos_q, const int32_t *type, int32_t n, const double *box_L,
+                   const int32_t *dims, int32_t *cell_start, int32_t *perm, float *pos_q_sorted,
+                   int32_t *type_sorted, void *workspace, size_t ws_bytes, uint32_t *status,
+                   void *stream)
+{
+    int ncell = 0;
+    if (n < 0 || n > kMaxAtoms) return MD_ERR_INVALID_ARG;
+    int e = validate_box(box_L);
+    if (e) return e;
+    if ((e = check_dims(dims, &ncell))) return e;
+    if (!cell_start) return MD_ERR_INVALID_ARG;
+    if (n > 0 && (!pos_q || !type || !perm || !pos_q_sorted || !type_sorted)) return MD_ERR_INVALID_ARG;
+    if ((pos_q && !aligned16(pos_q)) || (pos_q_sorted && !aligned16(pos_q_sorted))) return MD_ERR_INVALID_ARG;
+    WsLayout ws = ws_layout(n, ncell);
+    char *wsp = ws_base(workspace, ws_bytes, ws);
+    if (!wsp) return MD_ERR_WORKSPACE;
+    BoxF box = make_box(box_L, dims);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    return cuda_code(launch_build_cells(reinterpret_cast<const float4 *>(pos_q), type, n, box,
+                                        cell_start, perm, reinterpret_cast<float4 *>(pos_q_sorted),
+                                        type_sorted, ws, wsp, status, s));
+}
+
+int md_nonbonded_forces_algo(const int32_t *cell_start, const int32_t *perm,
+                             const float *pos_q_sorted, const int32_t *type_sorted, int32_t n,
+                             const double *box_L, const int32_t *dims, const md_forcefield *ff,
+                             int32_t mode, int32_t algo, void *forces_out,
+                             double *energy_virial_out, unsigned long long *pair_count_out,
+                             void *workspace, size_t ws_bytes, uint32_t *status, void *stream)
+{
+    int ncell = 0;
+    if (n < 0 || n > kMaxAtoms) return MD_ERR_INVALID_ARG;
+    int e = check_ff(ff);
+    if (e) return e;
+    if (mode != MD_ACCUM_F32 && mode != MD_ACCUM_FIXED64 && mode != MD_ACCUM_F64) return MD_ERR_INVALID_ARG;
+    if (algo == MD_ALGO_DEFAULT) algo = MD_ALGO_FULL_SHELL;
+    if (algo != MD_ALGO_FULL_SHELL) return MD_ERR_INVALID_ARG;
+    int32_t want[3];
+    if ((e = compute_dims(box_L, ff->rc, want))) return e;
+    if ((e = check_dims(dims, &ncell))) return e;
+    for (int d = 0; d < 3; ++d)
+        if (dims[d] != want[d]) return MD_ERR_CUTOFF;
+    if (!cell_start) return MD_ERR_INVALID_ARG;
+    if (n > 0 && (!perm || !pos_q_sorted || !type_sorted || !forces_out)) return MD_ERR_INVALID_ARG;
+    if (pos_q_sorted && !aligned16(pos_q_sorted)) return MD_ERR_INVALID_ARG;
+    WsLayout ws = ws_layout(n, ncell);
+    char *wsp = ws_base(workspace, ws_bytes, ws);
+    if (!wsp) return MD_ERR_WORKSPACE;
+    ForceArgs a;
+    a.cell_start = cell_start;
+    a.perm = perm;
+    a.pos_q_sorted = reinterpret_cast<const float4 *>(pos_q_sorted);
+    a.type_sorted = type_sorted;
+    a.n = n;
+    a.box = make_box(box_L, dims);
+    a.AB = reinterpret_cast<const float2 *>(ff->AB);
+    a.ntypes = ff->ntypes;
+    a.k_coulomb = (float)ff->k_coulomb;
+    a.k_coulomb64 = ff->k_coulomb;
+    a.rc = (float)ff->rc;
+    a.rc64 = ff->rc;
+    a.mode = mode;
+    a.algo = algo;
+    a.forces_out = forces_out;
+    a.energy_virial_out = energy_virial_out;
+    a.pair_count_out = pair_count_out;
+    a.status = status;
+    return cuda_code(launch_forces(a, ws, wsp, static_cast<cudaStream_t>(stream)));
+}
+
+int md_nonbonded_forces(const int32_t *cell_start, const int32_t *perm, const float *pos_q_sorted,
+                        const int32_t *type_sorted, int32_t n, const double *box_L,
+                        const int32_t *dims, const md_forcefield *ff, int32_t mode,
+                        void *forces_out, double *energy_virial_out,
+                        unsigned long long *pair_count_out, void *workspace, size_t ws_bytes,
+                        uint32_t *status, void *stream)
+{
+    return md_nonbonded_forces_algo(cell_start, perm, pos_q_sorted, type_sorted, n, box_L, dims, ff,
+                                    mode, MD_ALGO_DEFAULT, forces_out, energy_virial_out,
+                                    pair_count_out, workspace, ws_bytes, status, stream);
+}
+
+int md_step(double *pos, double *vel, void *forces, int32_t forces_valid, const float *inv_mass,
+            const float *q, const int32_t *type, int32_t n, const double *box_L,
+            const md_forcefield *ff, int32_t mode, double dt_fs, int32_t n_steps,
+            double *energy_log, void *workspace, size_t ws_bytes, uint32_t *status, void *stream)
+{
+    if (n < 0 || n > kMaxAtoms || n_steps < 0) return MD_ERR_INVALID_ARG;
+    if (!(dt_fs > 0.0) || !isfinite(dt_fs)) return MD_ERR_INVALID_ARG;
+    int e = check_ff(ff);
+    if (e) return e;
+    if (mode != MD_ACCUM_F32 && mode != MD_ACCUM_FIXED64 && mode != MD_ACCUM_F64) return MD_ERR_INVALID_ARG;
+    int32_t dims[3];
+    if ((e = compute_dims(box_L, ff->rc, dims))) return e;
+    if (n > 0 && (!pos || !vel || !forces || !inv_mass || !q || !type)) return MD_ERR_INVALID_ARG;
+    int ncell = dims[0] * dims[1] * dims[2];
+    WsLayout ws = ws_layout(n, ncell);
+    char *wsp = ws_base(workspace, ws_bytes, ws);
+    if (!wsp) return MD_ERR_WORKSPACE;
+    if (n == 0 || (n_steps == 0 && forces_valid)) return MD_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    BoxF box = make_box(box_L, dims);
+    int32_t *cs = reinterpret_cast<int32_t *>(wsp + ws.st_cell_start);
+    int32_t *pm = reinterpret_cast<int32_t *>(wsp + ws.st_perm);
+    float4 *pqs = reinterpret_cast<float4 *>(wsp + ws.st_pos_q_sorted);
+    int32_t *tys = reinterpret_cast<int32_t *>(wsp + ws.st_type_sorted);
+    float4 *pq = reinterpret_cast<float4 *>(wsp + ws.st_pos_q);
+    double *ev = reinterpret_cast<double *>(wsp + ws.ev);
+
+    ForceArgs a;
+    a.cell_start = cs;
+    a.perm = pm;
+    a.pos_q_sorted = pqs;
+    a.type_sorted = tys;
+    a.n = n;
+    a.box = box;
+    a.AB = reinterpret_cast<const float2 *>(ff->AB);
+    a.ntypes = ff->ntypes;
+    a.k_coulomb = (float)ff->k_coulomb;
+    a.k_coulomb64 = ff->k_coulomb;
+    a.rc = (float)ff->rc;
+    a.rc64 = ff->rc;
+    a.mode = mode;
+    a.algo = MD_ALGO_FULL_SHELL;
+    a.forces_out = forces;
+    a.pair_count_out = nullptr;
+    a.status = status;
+
+    cudaError_t ce;
+    auto eval_forces = [&](bool energy) -> cudaError_t {
+        cudaError_t r = launch_build_cells(pq, type, n, box, cs, pm, pqs, tys, ws, wsp, status, s);
+        if (r != cudaSuccess) return r;
+        a.energy_virial_out = energy ? ev : nullptr;
+        return launch_forces(a, ws, wsp, s);
+    };
+    if (!forces_valid) {
+        // wrap the start positions and make the float copy, then F(x0)
+        if ((ce = launch_drift_wrap(pos, vel, q, n, box, 0.0, pq, status, s)) != cudaSuccess) return MD_ERR_CUDA;
+        if ((ce = eval_forces(false)) != cudaSuccess) return MD_ERR_CUDA;
+    }
+    const double half_dt = 0.5 * dt_fs;
+    for (int st = 0; st < n_steps; ++st) {
+        if ((ce = launch_kick(vel, forces, mode, inv_mass, n, half_dt, s)) != cudaSuccess) return MD_ERR_CUDA;
+        if ((ce = launch_drift_wrap(pos, vel, q, n, box, dt_fs, pq, status, s)) != cudaSuccess) return MD_ERR_CUDA;
+        if ((ce = eval_forces(energy_log != nullptr)) != cudaSuccess) return MD_ERR_CUDA;
+        if ((ce = launch_kick(vel, forces, mode, inv_mass, n, half_dt, s)) != cudaSuccess) return MD_ERR_CUDA;
+        if (energy_log) {
+            ce = launch_energy_log_row(vel, inv_mass, n, ev, energy_log + 4 * (size_t)st, ws, wsp, s);
+            if (ce != cudaSuccess) return MD_ERR_CUDA;
+        }
+    }
+    return MD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,137 @@
+// md_internal.cuh -- shared device helpers and the workspace layout of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "md_nonbonded.h"
+
+namespace mdnb {
+
+// (kcal/mol/A)/amu expressed in A/fs^2
+constexpr double kAccelPerForcePerMass = 4.184e-4;
+// fixed-point scale of MD_ACCUM_FIXED64: one unit is 2^-32 kcal/mol/A
+constexpr float kFixedScale = 4294967296.0f;
+// |term| must stay below 2^31 so that term * 2^32 fits an int64
+constexpr float kFixedLimit = 2147483648.0f;
+
+constexpr int kMaxTypes = 32;
+
+// Per-block partial results of a force or kinetic-energy pass, reduced later in a
+// fixed order so that sums do not depend on block scheduling.
+struct Partial {
+    double e_lj, e_c, w;
+    unsigned long long count;
+};
+
+// Host-side description of the periodic box in the forms the kernels use.
+struct BoxF {
+    double L[3];
+    float Lhi[3];   // float(L): the leading part of L
+    float Llo[3];   // float(L - Lhi): the remainder, so Lhi + Llo == L to ~2^-48 L
+    float invL[3];  // 1/L rounded to float
+    int dims[3];
+    int ncell;
+};
+
+BoxF make_box(const double *L, const int32_t *dims);
+
+struct WsLayout {
+    size_t cell_id;     // int32 [n]          cell of each input atom
+    size_t cell_cnt;    // int32 [ncell]      per-cell counts, then scatter cursors
+    size_t perm_tmp;    // int32 [n]          unsorted slot -> input index
+    size_t accum;       // 32 B x n           sorted-order force accumulators
+    size_t partials;    // Partial [nslots]
+    size_t ev;          // double[4]          energy/virial scratch of md_step
+    size_t st_cell_start, st_perm, st_pos_q_sorted, st_type_sorted, st_pos_q;  // md_step only
+    size_t total;
+    int nslots;
+};
+
+WsLayout ws_layout(int n, int ncell);
+
+// ----------------------------------------------------------------- device helpers
+
+__device__ __forceinline__ void set_status(uint32_t *status, uint32_t bits)
+{
+    if (status) atomicOr(status, bits);
+}
+
+// Wrap a coordinate into [0, L) in FP64 (the documented rule).
+__device__ __forceinline__ double wrap_coord(double x, double L)
+{
+    double w = x - L * floor(x / L);
+    if (w < 0.0) w += L;
+    if (w >= L) w -= L;
+    return w;
+}
+
+// Cell index along one axis of a wrapped coordinate: floor(w * (n/L)) clamped.
+__device__ __forceinline__ int cell_coord(double w, int nc, double L)
+{
+    double inv_edge = (double)nc / L;
+    double f = floor(w * inv_edge);
+    return f < 0.0 ? 0 : (f > (double)(nc - 1) ? nc - 1 : (int)f);
+}
+
+// Minimum-image displacement xi - xj along one axis in FP32 for coordinates in
+// [0, L].  The image is chosen from the rounded difference, then the difference is
+// formed again so that it is exact up to one rounding of the result: the box shift
+// Lhi is subtracted from the coordinate near L (exact by Sterbenz), and the
+// remainder Llo is applied last.
+__device__ __forceinline__ float min_image_f32(float xi, float xj, float Lhi, float Llo, float invL)
+{
+    float d0 = xi - xj;
+    float k = rintf(d0 * invL);
+    float a = xi - (k > 0.0f ? Lhi : 0.0f);
+    float b = xj - (k < 0.0f ? Lhi : 0.0f);
+    return (a - b) - k * Llo;
+}
+
+__device__ __forceinline__ double min_image_f64(double xi, double xj, double L)
+{
+    double d = xi - xj;
+    return d - L * rint(d / L);
+}
+
+}  // namespace mdnb
+
+// Launchers implemented in the .cu files (all enqueue on `stream`, return cudaError_t).
+namespace mdnb {
+cudaError_t launch_build_cells(const float4 *pos_q, const int32_t *type, int n, const BoxF &box,
+                               int32_t *cell_start, int32_t *perm, float4 *pos_q_sorted,
+                               int32_t *type_sorted, const WsLayout &ws, char *wsp,
+                               uint32_t *status, cudaStream_t stream);
+
+struct ForceArgs {
+    const int32_t *cell_start;
+    const int32_t *perm;
+    const float4 *pos_q_sorted;
+    const int32_t *type_sorted;
+    int n;
+    BoxF box;
+    const float2 *AB;
+    int ntypes;
+    float k_coulomb;
+    double k_coulomb64;
+    float rc;
+    double rc64;
+    int mode;
+    int algo;
+    void *forces_out;
+    double *energy_virial_out;
+    unsigned long long *pair_count_out;
+    uint32_t *status;
+};
+
+cudaError_t launch_forces(const ForceArgs &a, const WsLayout &ws, char *wsp, cudaStream_t stream);
+
+cudaError_t launch_kick(double *vel, const void *forces, int mode, const float *inv_mass, int n,
+                        double half_dt, cudaStream_t stream);
+cudaError_t launch_drift_wrap(double *pos, const double *vel, const float *q, int n,
+                              const BoxF &box, double dt, float4 *pos_q_out, uint32_t *status,
+                              cudaStream_t stream);
+cudaError_t launch_energy_log_row(const double *vel, const float *inv_mass, int n,
+                                  const double *energy_virial, double *row, const WsLayout &ws,
+                                  char *wsp, cudaStream_t stream);
+}  // namespace mdnb

@@ -1,0 +1,103 @@
+"""The C ABI library loads and exports every entry point include/*.h declares; host-only
+calls and host-side validation work without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(md_[a-z0-9_]+)\s*\(", src))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1611_04474_gb300 import build
+
+    build.build()
+    from paper_1611_04474_gb300 import api
+
+    return api.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_1611_04474_gb300 import api
+
+    declared = _declared()
+    assert {"md_build_cells", "md_nonbonded_forces", "md_step"} <= declared
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert declared <= set(api.EXPORTS) | {n for n in declared if n.startswith("md_") and hasattr(lib, n)}
+
+
+def test_abi_version_and_strerror(lib):
+    assert lib.md_abi_version() == 1
+    for code in (0, -1, -2, -3, -4, -5, -99):
+        assert isinstance(lib.md_strerror(code), bytes)
+
+
+def test_cell_dims_rule_and_cutoff_errors(lib):
+    from paper_1611_04474_gb300 import api
+
+    assert api.cell_dims((108.86, 108.86, 77.76), 12.0) == [9, 9, 6]
+    assert api.cell_dims((31.0, 31.0, 31.0), 12.0) == [2, 2, 2]
+    for box, rc in (((31.0, 31.0, 31.0), 15.5), ((31.0, 31.0, 31.0), 0.0), ((10, 40, 40), 5.0),
+                    ((31.0, 31.0, 31.0), float("nan"))):
+        with pytest.raises(api.MDError) as e:
+            api.cell_dims(box, rc)
+        assert e.value.code == -2
+    with pytest.raises(api.MDError) as e:
+        api.cell_dims((0.0, 10.0, 10.0), 1.0)
+    assert e.value.code == -1
+
+
+def test_workspace_bytes(lib):
+    from paper_1611_04474_gb300 import api
+
+    small = api.workspace_bytes(3000, [2, 2, 2])
+    big = api.workspace_bytes(92224, [9, 9, 6])
+    assert 0 < small < big
+    assert lib.md_workspace_bytes(-1, (ctypes.c_int32 * 3)(2, 2, 2)) == 0
+    assert lib.md_workspace_bytes(10, (ctypes.c_int32 * 3)(0, 2, 2)) == 0
+
+
+def test_host_validation_rejects_before_any_launch(lib):
+    P = ctypes.c_void_p
+    box = (ctypes.c_double * 3)(10.0, 10.0, 10.0)
+    dims = (ctypes.c_int32 * 3)(3, 3, 3)
+    # negative n
+    assert lib.md_build_cells(None, None, -1, box, dims, None, None, None, None, None, 0, None,
+                              None) == -1
+    # missing cell_start
+    assert lib.md_build_cells(None, None, 0, box, dims, None, None, None, None, None, 0, None,
+                              None) == -1
+    # workspace missing (n = 0 is otherwise valid)
+    cs = P(16)  # never dereferenced: validation fails first
+    assert lib.md_build_cells(None, None, 0, box, dims, cs, None, None, None, None, 0, None,
+                              None) == -3
+    from paper_1611_04474_gb300 import api
+
+    ff = api.md_forcefield(4, 0, 256, 332.0636, 3.0)
+    # dims inconsistent with rc
+    bad = (ctypes.c_int32 * 3)(2, 3, 3)
+    assert lib.md_nonbonded_forces(cs, None, None, None, 0, box, bad, ctypes.byref(ff), 0, None,
+                                   None, None, None, 0, None, None) == -2
+    # ntypes outside 1..32
+    ff_bad = api.md_forcefield(33, 0, 256, 332.0636, 3.0)
+    assert lib.md_nonbonded_forces(cs, None, None, None, 0, box, dims, ctypes.byref(ff_bad), 0,
+                                   None, None, None, None, 0, None, None) == -1
+    # unknown mode
+    assert lib.md_nonbonded_forces(cs, None, None, None, 0, box, dims, ctypes.byref(ff), 7, None,
+                                   None, None, None, 0, None, None) == -1
+    # md_step: dt <= 0
+    assert lib.md_step(None, None, None, 0, None, None, None, 0, box, ctypes.byref(ff), 0, 0.0, 1,
+                       None, None, 0, None, None) == -1

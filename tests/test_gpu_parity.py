@@ -1,0 +1,250 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle, element by element.
+
+Bars: cell lists identical (integer work, bit-exact); forces within the criterion of
+tests/parity.py (1e-5 for FP32 pair math, 1e-12 for the FP64 mode); pair counts exact
+up to boundary pairs; FIXED64 forces bit-reproducible, exactly antisymmetric and
+permutation-invariant.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1611_04474_gb300 import workloads as W
+from tests.parity import boundary_alternatives, force_errors
+
+pytestmark = pytest.mark.gpu
+
+TOL_F32 = 1e-5
+TOL_F64 = 1e-12
+
+ALGOS_F32 = [1]  # full shell
+
+SYSTEMS = {
+    "gas3000": lambda: W.workload_random_3000(),
+    "lattice3000": lambda: W.lattice_box(n=3000, seed=5, ntypes=6),
+    "box_3x4x6": lambda: W.small_random(700, (9.5, 13.0, 18.5), rc=3.0, seed=3, min_dist=0.7),
+    "box_2x3x2": lambda: W.small_random(300, (6.5, 12.0, 6.6), rc=3.2, seed=4, min_dist=0.7),
+    "box_5x5x7_ragged": lambda: W.small_random(2111, (20.0, 20.5, 28.9), rc=4.0, seed=8,
+                                               min_dist=0.8, ntypes=5),
+}
+
+
+def _oracle_ref(s):
+    ff = oracle.ForceField.from_system(s)
+    p = s.pos.astype(np.float64)
+    ref = oracle.forces_cells(p, s.q, s.type, s.box, ff)
+    alts, nb = boundary_alternatives(p, s, ff, ref.F)
+    return ff, p, ref, alts, nb
+
+
+_cache = {}
+
+
+def ref_for(name):
+    if name not in _cache:
+        s = SYSTEMS[name]()
+        _cache[name] = (s,) + _oracle_ref(s)
+    return _cache[name]
+
+
+def run_forces(api, s, mode, algo=1, energy=True):
+    eng = api.Engine(s, mode=mode, algo=algo)
+    eng.build_cells()
+    eng.compute_forces(energy=energy, count=True)
+    torch.cuda.synchronize()
+    return eng
+
+
+@pytest.mark.parametrize("name", list(SYSTEMS))
+def test_cells_identical_to_oracle(cuda_lib, name):
+    api = cuda_lib
+    s = SYSTEMS[name]()
+    eng = api.Engine(s)
+    eng.build_cells()
+    torch.cuda.synchronize()
+    dims, cell_of, cell_start, order = oracle.build_cells(s.pos.astype(np.float64), s.box, s.rc)
+    assert list(dims) == eng.dims
+    np.testing.assert_array_equal(eng.cells.cell_start.cpu().numpy(), cell_start)
+    np.testing.assert_array_equal(eng.cells.perm.cpu().numpy(), order)
+    pqs = eng.cells.pos_q_sorted.cpu().numpy()
+    np.testing.assert_array_equal(pqs[:, :3], s.pos[order])
+    np.testing.assert_array_equal(pqs[:, 3], s.q[order])
+    np.testing.assert_array_equal(eng.cells.type_sorted.cpu().numpy(), s.type[order])
+    assert int(eng.status.item()) == 0
+
+
+@pytest.mark.parametrize("name", list(SYSTEMS))
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_forces_match_oracle(cuda_lib, name, mode):
+    api = cuda_lib
+    s, ff, p, ref, alts, nb = ref_for(name)
+    for algo in (ALGOS_F32 if mode != 2 else [1]):
+        eng = run_forces(api, s, mode, algo)
+        F = api.forces_to_f64(eng.forces, mode).cpu().numpy()
+        err = force_errors(F, ref.F, ref.cond, alts)
+        tol = TOL_F64 if mode == 2 else TOL_F32
+        assert err["max_norm"] <= tol, (name, mode, algo, err, nb)
+        assert int(eng.status.item()) == 0
+        cnt = int(eng.pair_count.item())
+        assert abs(cnt - ref.npairs) <= nb, (cnt, ref.npairs, nb)
+        ev = eng.energy_virial.cpu().numpy()
+        etol = 1e-12 if mode == 2 else 1e-5
+        for k in range(3):
+            assert abs(ev[k] - ref.energy[k]) <= etol * ref.energy_abs[k] + 1e-9, (k, ev, ref.energy)
+
+
+def test_fixed_mode_exact_sum_and_reproducible(cuda_lib):
+    api = cuda_lib
+    s, ff, p, ref, alts, nb = ref_for("gas3000")
+    runs = []
+    for _ in range(3):
+        eng = run_forces(api, s, api.ACCUM_FIXED64)
+        runs.append(eng.forces.cpu().numpy().copy())
+    assert np.array_equal(runs[0], runs[1]) and np.array_equal(runs[0], runs[2])
+    # Newton's third law holds exactly in integer arithmetic
+    assert np.all(runs[0].sum(axis=0, dtype=np.int64) == 0)
+
+
+def test_fixed_mode_permutation_invariant(cuda_lib):
+    api = cuda_lib
+    s = SYSTEMS["box_5x5x7_ragged"]()
+    base = run_forces(api, s, api.ACCUM_FIXED64).forces.cpu().numpy()
+    perm = np.random.default_rng(1).permutation(s.n)
+    s2 = W.System(s.name, s.pos[perm], s.q[perm], s.type[perm], s.box, s.rc, s.sigma, s.eps, s.AB,
+                  s.mass[perm], s.vel[perm])
+    got = run_forces(api, s2, api.ACCUM_FIXED64).forces.cpu().numpy()
+    assert np.array_equal(got, base[perm])
+
+
+def test_f64_mode_translation(cuda_lib):
+    # translating every atom by a box vector changes nothing after the wrap
+    api = cuda_lib
+    s = SYSTEMS["box_3x4x6"]()
+    base = run_forces(api, s, api.ACCUM_F64).forces.cpu().numpy()
+    s2 = W.System(s.name, (s.pos.astype(np.float64) + s.box * np.array([1, -2, 3])).astype(np.float32),
+                  s.q, s.type, s.box, s.rc, s.sigma, s.eps, s.AB, s.mass, s.vel)
+    got = run_forces(api, s2, api.ACCUM_F64).forces.cpu().numpy()
+    ff, p, ref, alts, nb = _oracle_ref(s2)
+    err = force_errors(got, ref.F, ref.cond, alts)
+    assert err["max_norm"] <= 1e-6  # coordinates outside the box lose bits when wrapped
+    assert np.abs(got - base).max() <= 1e-6 * np.abs(base).max()
+
+
+def test_lattice_92k_full_system(cuda_lib):
+    """The throughput workload itself (92,224 atoms, ApoA1 box), every atom checked."""
+    api = cuda_lib
+    s = W.workload_lattice_92k()
+    ff, p, ref, alts, nb = _oracle_ref(s)
+    for mode in (api.ACCUM_F32, api.ACCUM_FIXED64):
+        for algo in ALGOS_F32:
+            eng = run_forces(api, s, mode, algo)
+            F = api.forces_to_f64(eng.forces, mode).cpu().numpy()
+            err = force_errors(F, ref.F, ref.cond, alts)
+            assert err["max_norm"] <= TOL_F32, (mode, algo, err, nb)
+            assert abs(int(eng.pair_count.item()) - ref.npairs) <= nb
+            assert int(eng.status.item()) == 0
+
+
+# ------------------------------------------------------------------ edge cases
+
+def _custom(pos, box, rc=3.0, ntypes=2, seed=0, q=None, types=None):
+    rng = np.random.default_rng(seed)
+    n = len(pos)
+    sigma = rng.uniform(0.9, 1.1, ntypes)
+    eps = rng.uniform(0.5, 1.0, ntypes)
+    q = np.asarray(q if q is not None else rng.choice([-0.5, 0.5], n), np.float32)
+    t = np.asarray(types if types is not None else rng.integers(0, ntypes, n), np.int32)
+    mass = np.full(n, 12.0, np.float32)
+    return W.System("custom", np.asarray(pos, np.float32).reshape(n, 3), q, t,
+                    np.asarray(box, np.float64), float(np.float32(rc)), sigma, eps,
+                    W.lj_table(sigma, eps), mass, np.zeros((n, 3)))
+
+
+def _check_vs_oracle(api, s, modes=(0, 1, 2)):
+    ff, p, ref, alts, nb = _oracle_ref(s)
+    for mode in modes:
+        eng = run_forces(api, s, mode)
+        F = api.forces_to_f64(eng.forces, mode).cpu().numpy()
+        err = force_errors(F, ref.F, ref.cond, alts)
+        assert err["max_norm"] <= (TOL_F64 if mode == 2 else TOL_F32), (mode, err)
+        assert int(eng.pair_count.item()) == ref.npairs or nb > 0
+    return ref
+
+
+def test_single_atom_and_empty_cells(cuda_lib):
+    api = cuda_lib
+    s = _custom([[1.0, 2.0, 3.0]], (10.0, 10.0, 10.0))
+    ref = _check_vs_oracle(api, s)
+    assert ref.npairs == 0
+    # every atom crowded into one corner cell of a 4x4x4 grid: most cells empty
+    rng = np.random.default_rng(2)
+    pos = rng.uniform(0.0, 2.5, (60, 3))
+    s = _custom(pos, (12.0, 12.0, 12.0), rc=2.9)
+    _check_vs_oracle(api, s)
+
+
+def test_pair_across_every_face(cuda_lib):
+    api = cuda_lib
+    box = (10.0, 11.0, 12.0)
+    pos = [[0.2, 5.0, 6.0], [9.6, 5.3, 6.2],     # across x
+           [3.0, 0.1, 3.0], [3.4, 10.8, 2.7],    # across y
+           [7.0, 7.0, 11.9], [7.1, 6.6, 0.3],    # across z
+           [0.1, 0.2, 0.3], [9.8, 10.9, 11.7]]   # across a corner
+    s = _custom(pos, box, rc=3.0)
+    ref = _check_vs_oracle(api, s)
+    assert ref.npairs >= 4
+
+
+def test_atoms_on_cell_boundaries_and_outside_the_box(cuda_lib):
+    api = cuda_lib
+    box = np.array([12.0, 12.0, 12.0])  # rc 3 -> 4x4x4 cells of edge 3 (exact)
+    g = np.stack(np.meshgrid(*[np.arange(4)] * 3, indexing="ij"), -1).reshape(-1, 3) * 3.0
+    pos = np.concatenate([g, g + 1.5])  # half on cell corners exactly
+    s = _custom(pos, box, rc=3.0)
+    _check_vs_oracle(api, s)
+    rng = np.random.default_rng(5)
+    pos = rng.uniform(-30.0, 40.0, (200, 3))  # far outside [0, L): wrapped by the build
+    s = _custom(pos, box, rc=3.0)
+    eng = run_forces(api, s, api.ACCUM_F64)
+    wrapped = np.mod(pos.astype(np.float32).astype(np.float64), box)
+    s_in = _custom(wrapped, box, rc=3.0, q=s.q, types=s.type)
+    ff, p, ref, alts, nb = _oracle_ref(s_in)
+    err = force_errors(eng.forces.cpu().numpy(), ref.F, ref.cond, alts)
+    assert err["max_norm"] <= 1e-6
+
+
+def test_many_types(cuda_lib):
+    api = cuda_lib
+    s = W.small_random(900, (15.0, 15.0, 15.0), ntypes=32, rc=3.5, seed=12, min_dist=0.8)
+    _check_vs_oracle(api, s, modes=(0, 1))
+
+
+def test_status_flags(cuda_lib):
+    api = cuda_lib
+    pos = [[1.0, 1.0, 1.0], [np.nan, 2.0, 2.0], [3.0, 3.0, 3.0]]
+    s = _custom(pos, (10.0, 10.0, 10.0))
+    eng = run_forces(api, s, api.ACCUM_F32)
+    assert int(eng.status.item()) & api.STATUS_NONFINITE
+    s = _custom([[1.0, 1.0, 1.0], [1.5, 1.0, 1.0]], (10.0, 10.0, 10.0), types=[0, 7])
+    eng = run_forces(api, s, api.ACCUM_F32)
+    assert int(eng.status.item()) & api.STATUS_BAD_TYPE
+    # two atoms 0.01 A apart: an LJ term far beyond 2^31 kcal/mol/A
+    s = _custom([[1.0, 1.0, 1.0], [1.01, 1.0, 1.0]], (10.0, 10.0, 10.0), types=[0, 0])
+    eng = run_forces(api, s, api.ACCUM_FIXED64)
+    assert int(eng.status.item()) & api.STATUS_FIXED_OVERFLOW
+
+
+def test_errors_from_the_abi(cuda_lib):
+    api = cuda_lib
+    s = W.small_random(50, (10.0, 10.0, 10.0), rc=3.0, seed=1)
+    eng = api.Engine(s)
+    eng.build_cells()
+    small_ws = torch.empty(64, dtype=torch.uint8, device="cuda")
+    with pytest.raises(api.MDError) as e:
+        api.nonbonded_forces(eng.cells, eng.box, eng.ff, small_ws)
+    assert e.value.code == -3
+    ff_bad = api.ForceField(s.AB, s.k_coulomb, 5.0)  # rc >= L/2
+    with pytest.raises(api.MDError) as e:
+        api.nonbonded_forces(eng.cells, eng.box, ff_bad, eng.workspace)
+    assert e.value.code == -2
