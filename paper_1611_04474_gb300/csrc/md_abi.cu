@@ -99,7 +99,7 @@ WsLayout ws_layout(int n, int ncell)
     WsLayout w;
     size_t nn = (size_t)(n > 0 ? n : 1);
     size_t nc = (size_t)(ncell > 0 ? ncell : 1);
-    int slots = ncell;
+    int slots = 27 * ncell;  // one partial per CTA of the half-shell kernel at most
     int kin = (int)((nn + 255) / 256);
     if (slots < kin) slots = kin;
     if (slots < 2048) slots = 2048;
@@ -189,8 +189,8 @@ int md_nonbonded_forces_algo(const int32_t *cell_start, const int32_t *perm,
     int e = check_ff(ff);
     if (e) return e;
     if (mode != MD_ACCUM_F32 && mode != MD_ACCUM_FIXED64 && mode != MD_ACCUM_F64) return MD_ERR_INVALID_ARG;
-    if (algo == MD_ALGO_DEFAULT) algo = MD_ALGO_FULL_SHELL;
-    if (algo != MD_ALGO_FULL_SHELL) return MD_ERR_INVALID_ARG;
+    if (algo != MD_ALGO_DEFAULT && algo != MD_ALGO_FULL_SHELL && algo != MD_ALGO_HALF_SHELL)
+        return MD_ERR_INVALID_ARG;
     int32_t want[3];
     if ((e = compute_dims(box_L, ff->rc, want))) return e;
     if ((e = check_dims(dims, &ncell))) return e;
@@ -277,7 +277,7 @@ int md_step(double *pos, double *vel, void *forces, int32_t forces_valid, const 
     a.rc = (float)ff->rc;
     a.rc64 = ff->rc;
     a.mode = mode;
-    a.algo = MD_ALGO_FULL_SHELL;
+    a.algo = MD_ALGO_DEFAULT;
     a.forces_out = forces;
     a.pair_count_out = nullptr;
     a.status = status;

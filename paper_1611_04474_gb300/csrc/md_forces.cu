@@ -13,63 +13,6 @@
 
 namespace mdnb {
 
-__device__ __forceinline__ long long to_fixed(float v, uint32_t *status)
-{
-    if (!(fabsf(v) < kFixedLimit)) {
-        set_status(status, isfinite(v) ? MD_STATUS_FIXED_OVERFLOW : MD_STATUS_NONFINITE);
-        return 0;
-    }
-    return __float2ll_rn(v * kFixedScale);
-}
-
-__device__ __forceinline__ int clamp_type(int t, int ntypes, uint32_t *status)
-{
-    if ((unsigned)t >= (unsigned)ntypes) {
-        set_status(status, MD_STATUS_BAD_TYPE);
-        return 0;
-    }
-    return t;
-}
-
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Sum (e_lj, e_c, w, count) over the block into partials[blockIdx.x] in a fixed order.
-template <int kThreads>
-__device__ __forceinline__ void block_partial(double e_lj, double e_c, double w,
-                                              unsigned long long cnt, Partial *partials)
-{
-    __shared__ double s_e[3][kThreads / 32];
-    __shared__ unsigned long long s_c[kThreads / 32];
-    e_lj = warp_sum(e_lj);
-    e_c = warp_sum(e_c);
-    w = warp_sum(w);
-    cnt = warp_sum(cnt);
-    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) {
-        s_e[0][warp] = e_lj;
-        s_e[1][warp] = e_c;
-        s_e[2][warp] = w;
-        s_c[warp] = cnt;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        Partial p = {0.0, 0.0, 0.0, 0ull};
-        for (int k = 0; k < kThreads / 32; ++k) {
-            p.e_lj += s_e[0][k];
-            p.e_c += s_e[1][k];
-            p.w += s_e[2][k];
-            p.count += s_c[k];
-        }
-        partials[blockIdx.x] = p;
-    }
-}
-
 namespace {
 
 constexpr int kFullThreads = 128;
@@ -260,25 +203,33 @@ cudaError_t launch_forces(const ForceArgs &a, const WsLayout &ws, char *wsp, cud
 {
     Partial *partials = reinterpret_cast<Partial *>(wsp + ws.partials);
     const bool energy = a.energy_virial_out != nullptr;
-    size_t elem = a.mode == MD_ACCUM_F32 ? sizeof(float) : 8;
     if (a.n == 0) {
         // nothing to evaluate: zero outputs
         if (a.energy_virial_out) cudaMemsetAsync(a.energy_virial_out, 0, 3 * sizeof(double), stream);
         if (a.pair_count_out) cudaMemsetAsync(a.pair_count_out, 0, sizeof(unsigned long long), stream);
         return cudaGetLastError();
     }
-    (void)elem;
-    switch (a.mode * 2 + (energy ? 1 : 0)) {
-    case MD_ACCUM_F32 * 2 + 0: launch_full<MD_ACCUM_F32, false>(a, partials, stream); break;
-    case MD_ACCUM_F32 * 2 + 1: launch_full<MD_ACCUM_F32, true>(a, partials, stream); break;
-    case MD_ACCUM_FIXED64 * 2 + 0: launch_full<MD_ACCUM_FIXED64, false>(a, partials, stream); break;
-    case MD_ACCUM_FIXED64 * 2 + 1: launch_full<MD_ACCUM_FIXED64, true>(a, partials, stream); break;
-    case MD_ACCUM_F64 * 2 + 0: launch_full<MD_ACCUM_F64, false>(a, partials, stream); break;
-    case MD_ACCUM_F64 * 2 + 1: launch_full<MD_ACCUM_F64, true>(a, partials, stream); break;
-    default: return cudaErrorInvalidValue;
+    // the FP64 reference mode always runs the full-shell kernel
+    int algo = a.algo;
+    if (algo == MD_ALGO_DEFAULT || a.mode == MD_ACCUM_F64)
+        algo = a.mode == MD_ACCUM_F64 ? MD_ALGO_FULL_SHELL : MD_ALGO_HALF_SHELL;
+    int nblocks = a.box.ncell;
+    if (algo == MD_ALGO_HALF_SHELL) {
+        cudaError_t e = launch_half_shell(a, ws, wsp, partials, &nblocks, stream);
+        if (e != cudaSuccess) return e;
+    } else {
+        switch (a.mode * 2 + (energy ? 1 : 0)) {
+        case MD_ACCUM_F32 * 2 + 0: launch_full<MD_ACCUM_F32, false>(a, partials, stream); break;
+        case MD_ACCUM_F32 * 2 + 1: launch_full<MD_ACCUM_F32, true>(a, partials, stream); break;
+        case MD_ACCUM_FIXED64 * 2 + 0: launch_full<MD_ACCUM_FIXED64, false>(a, partials, stream); break;
+        case MD_ACCUM_FIXED64 * 2 + 1: launch_full<MD_ACCUM_FIXED64, true>(a, partials, stream); break;
+        case MD_ACCUM_F64 * 2 + 0: launch_full<MD_ACCUM_F64, false>(a, partials, stream); break;
+        case MD_ACCUM_F64 * 2 + 1: launch_full<MD_ACCUM_F64, true>(a, partials, stream); break;
+        default: return cudaErrorInvalidValue;
+        }
     }
     if (a.energy_virial_out || a.pair_count_out)
-        k_reduce_partials<<<1, 256, 0, stream>>>(partials, a.box.ncell, a.energy_virial_out,
+        k_reduce_partials<<<1, 256, 0, stream>>>(partials, nblocks, a.energy_virial_out,
                                                  a.pair_count_out);
     return cudaGetLastError();
 }

@@ -94,6 +94,65 @@ __device__ __forceinline__ double min_image_f64(double xi, double xj, double L)
     return d - L * rint(d / L);
 }
 
+// Round one pair-force component to the MD_ACCUM_FIXED64 grid (2^-32 kcal/mol/A),
+// round-to-nearest-even; flags terms that do not fit and contributes nothing for them.
+__device__ __forceinline__ long long to_fixed(float v, uint32_t *status)
+{
+    if (!(fabsf(v) < kFixedLimit)) {
+        set_status(status, isfinite(v) ? MD_STATUS_FIXED_OVERFLOW : MD_STATUS_NONFINITE);
+        return 0;
+    }
+    return __float2ll_rn(v * kFixedScale);
+}
+
+__device__ __forceinline__ int clamp_type(int t, int ntypes, uint32_t *status)
+{
+    if ((unsigned)t >= (unsigned)ntypes) {
+        set_status(status, MD_STATUS_BAD_TYPE);
+        return 0;
+    }
+    return t;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum (e_lj, e_c, w, count) over the block into partials[blockIdx.x] in a fixed order.
+template <int kThreads>
+__device__ __forceinline__ void block_partial(double e_lj, double e_c, double w,
+                                              unsigned long long cnt, Partial *partials)
+{
+    __shared__ double s_e[3][kThreads / 32];
+    __shared__ unsigned long long s_c[kThreads / 32];
+    e_lj = warp_sum(e_lj);
+    e_c = warp_sum(e_c);
+    w = warp_sum(w);
+    cnt = warp_sum(cnt);
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        s_e[0][warp] = e_lj;
+        s_e[1][warp] = e_c;
+        s_e[2][warp] = w;
+        s_c[warp] = cnt;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Partial p = {0.0, 0.0, 0.0, 0ull};
+        for (int k = 0; k < kThreads / 32; ++k) {
+            p.e_lj += s_e[0][k];
+            p.e_c += s_e[1][k];
+            p.w += s_e[2][k];
+            p.count += s_c[k];
+        }
+        partials[blockIdx.x] = p;
+    }
+}
+
 }  // namespace mdnb
 
 // Launchers implemented in the .cu files (all enqueue on `stream`, return cudaError_t).
@@ -125,6 +184,9 @@ struct ForceArgs {
 };
 
 cudaError_t launch_forces(const ForceArgs &a, const WsLayout &ws, char *wsp, cudaStream_t stream);
+int half_shell_pairs_per_cell(const BoxF &box);
+cudaError_t launch_half_shell(const ForceArgs &a, const WsLayout &ws, char *wsp, Partial *partials,
+                              int *nblocks_out, cudaStream_t stream);
 
 cudaError_t launch_kick(double *vel, const void *forces, int mode, const float *inv_mass, int n,
                         double half_dt, cudaStream_t stream);
