@@ -95,17 +95,14 @@ k_full_shell(const int32_t *__restrict__ cell_start, const int32_t *__restrict__
                     float dx = min_image_f32(pi.x, pj.x, box.Lhi[0], box.Llo[0], box.invL[0]);
                     float dy = min_image_f32(pi.y, pj.y, box.Lhi[1], box.Llo[1], box.invL[1]);
                     float dz = min_image_f32(pi.z, pj.z, box.Lhi[2], box.Llo[2], box.invL[2]);
-                    float r2 = dx * dx + dy * dy + dz * dz;
+                    float r2 = pair_r2(dx, dy, dz);
                     if (!(r2 < rc2f)) continue;
                     const int tj = clamp_type(ty[b], ntypes, status);
                     const float2 ab = sAB[ti * ntypes + tj];
-                    float kqq = kc * pi.w * pj.w;
-                    float ir2 = __frcp_rn(r2);
-                    float ir = rsqrtf(r2);
-                    float ir6 = ir2 * ir2 * ir2;
-                    float ir8 = ir6 * ir2;
-                    float f = ab.x * (ir8 * ir6) - ab.y * ir8 + kqq * ir2 * ir;
-                    float Fx = f * dx, Fy = f * dy, Fz = f * dz;
+                    float kqq = __fmul_rn(kc, __fmul_rn(pi.w, pj.w));
+                    float ir, ir2, ir6;
+                    float f = pair_f(r2, ab.x, ab.y, kqq, ir, ir2, ir6);
+                    float Fx = __fmul_rn(f, dx), Fy = __fmul_rn(f, dy), Fz = __fmul_rn(f, dz);
                     if (MODE == MD_ACCUM_FIXED64) {
                         ix += to_fixed(Fx, status);
                         iy += to_fixed(Fy, status);
@@ -116,7 +113,7 @@ k_full_shell(const int32_t *__restrict__ cell_start, const int32_t *__restrict__
                         fz += Fz;
                     }
                     if (ENERGY) {
-                        e_lj += 0.5 * (double)(ab.x * (1.0f / 12.0f) * (ir6 * ir6) - ab.y * (1.0f / 6.0f) * ir6);
+                        e_lj += 0.5 * (double)pair_u_lj(ab.x, ab.y, ir6);
                         e_c += 0.5 * (double)(kqq * ir);
                         vir += 0.5 * (double)(f * r2);
                     }

@@ -5,18 +5,22 @@
 // plus 13 forward neighbours), and the reaction -F goes to the neighbour atom
 // (Newton's third law).  The two stages of the paper's enhanced accelerator
 // (Section V.B: cheap distance filters feeding one expensive force unit through a
-// FIFO) become, inside one warp:
-//   filter:  32 home atoms (one per lane) x 32 neighbour atoms (broadcast from shared
-//            memory); each lane folds the sign of rc'^2 - r^2 of its 32 candidates
-//            into a bit mask with one funnel shift per candidate;
-//   compact: popcount + warp prefix sum place the surviving (i, j) pairs in a per-warp
-//            queue in shared memory;
+// FIFO) become, inside one warp and one 32x32 item (32 home rows x 32 neighbour
+// columns):
+//   filter:  each lane holds one home atom; the 32 neighbour atoms are broadcast from
+//            shared memory; the sign of rc'^2 - r^2 of every candidate is folded into
+//            a 32-bit row mask with one funnel shift;
+//   compact: a popcount prefix sum over the rows gives each row its offset, and the
+//            surviving (row, column) pairs are written contiguously per row;
 //   force:   full warps of 32 survivors evaluate Eq. 1 + Eq. 2, so a low survival rate
 //            does not idle lanes of the force math.  The exact test r^2 < rc^2 is
 //            applied here; the filter uses rc'^2 = rc^2 + a tiny margin so that it
-//            never rejects a pair the exact test keeps.
-// Forces on both atoms of a pair are summed in shared memory per tile, then added to
-// sorted-order accumulators in global memory with one vector atomic per atom per tile.
+//            never rejects a pair the exact test keeps;
+//   reduce:  each lane sums its own row's contiguous pair forces into registers (the
+//            i-side, kept across the whole row block); the survival matrix is
+//            transposed with warp shuffles so that each lane gathers its column's
+//            pair forces (the j-side reaction) into warp-private shared arrays.
+// No atomics are used until a tile is finished; then one vector atomic per atom.
 //
 // Periodic images: for an axis with >= 3 cells the neighbour cell's image is fixed by
 // the stencil offset.  The box length L = Lhi + Llo (float + remainder); the coordinate
@@ -34,7 +38,6 @@ namespace {
 constexpr int kHW = 4;               // warps per CTA
 constexpr int kHT = kHW * 32;        // threads per CTA
 constexpr int kTile = 256;           // atoms of a cell staged at once (i, j indices fit 8 bits)
-constexpr int kQCap = 1024 + 64;     // survivor queue per warp: one 32x32 item + leftovers
 constexpr float kFar = 1.0e18f;      // coordinate of padding slots: fails every filter
 
 __constant__ int kForward[13][3] = {{1, 0, 0},   {-1, 1, 0}, {0, 1, 0},  {1, 1, 0},  {-1, -1, 1},
@@ -153,20 +156,47 @@ struct HalfArgs {
     uint32_t *status;
 };
 
+// 32x32 bit-matrix transpose across a warp: lane l holds row l (bit k = M[l][k]) on
+// entry and column l (bit k = M[k][l]) on exit.
+__device__ __forceinline__ unsigned transpose32(unsigned x, int lane)
+{
+    const unsigned lo[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int t = 0; t < 5; ++t) {
+        const int s = 16 >> t;
+        const unsigned y = __shfl_xor_sync(0xffffffffu, x, s);
+        x = (lane & s) ? ((x & ~lo[t]) | ((y & ~lo[t]) >> s)) : ((x & lo[t]) | ((y & lo[t]) << s));
+    }
+    return x;
+}
+
+template <int MODE>
+struct KCap {
+    static constexpr int value = MODE == MD_ACCUM_FIXED64 ? 128 : 192;  // survivors buffered per pass
+};
+
 template <int MODE, bool ENERGY, bool MI>
-__global__ void __launch_bounds__(kHT, 4) k_half_shell(HalfArgs a)
+__global__ void __launch_bounds__(kHT, 6) k_half_shell(HalfArgs a)
 {
     using Acc = typename AccT<MODE>::T;
+    constexpr int CAP = KCap<MODE>::value;
     __shared__ float4 s_hp[kTile];
     __shared__ float4 s_np[kTile];
     __shared__ int s_ht[kTile];
     __shared__ int s_nt[kTile];
-    __shared__ Acc s_hf[3][kTile];
-    __shared__ Acc s_nf[3][kTile];
-    __shared__ uint16_t s_q[kHW][kQCap];
-    __shared__ float2 s_ab[kMaxTypes * kMaxTypes];
+    __shared__ Acc s_hf[3][kTile];          // home atoms: i-side sums of the whole cell pair
+    __shared__ uint16_t s_q[kHW][CAP];      // per-warp (row, column) of the buffered pairs
+    __shared__ unsigned s_keep[kHW][32];
+    __shared__ int s_rs[kHW][32];
+    // dynamic: per-warp j-side sums of the current tile [kHW][3][kTile], per-warp pair
+    // forces of the current item pass [kHW][3][CAP], the LJ table [ntypes * ntypes]
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    Acc(*s_nf)[3][kTile] = reinterpret_cast<Acc(*)[3][kTile]>(s_dyn);
+    Acc(*s_fb)[3][CAP] = reinterpret_cast<Acc(*)[3][CAP]>(s_dyn + sizeof(Acc) * kHW * 3 * kTile);
+    float2 *s_ab = reinterpret_cast<float2 *>(s_dyn + sizeof(Acc) * kHW * 3 * (kTile + CAP));
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
     const int T = a.ntypes;
     float e_lj = 0.f, e_c = 0.f, vir = 0.f;
     unsigned long long cnt = 0;
@@ -185,6 +215,8 @@ __global__ void __launch_bounds__(kHT, 4) k_half_shell(HalfArgs a)
     }
     for (int t = threadIdx.x; t < T * T; t += kHT) s_ab[t] = a.AB[t];
     uint16_t *q = s_q[warp];
+    Acc(*fb)[CAP] = s_fb[warp];
+    Acc(*nfw)[kTile] = s_nf[warp];
 
     for (int h0 = 0; h0 < nh; h0 += kTile) {
         const int mh = min(kTile, nh - h0);
@@ -222,147 +254,169 @@ __global__ void __launch_bounds__(kHT, 4) k_half_shell(HalfArgs a)
                         p.z -= g.ns[2];
                         ty = clamp_type(a.ty[n_begin + n0 + t], T, a.status);
                     } else {
-                        p = make_float4(kFar, kFar, kFar, 0.f);
+                        p = make_float4(-kFar, -kFar, -kFar, 0.f);
                     }
                     s_np[t] = p;
                     s_nt[t] = ty;
-                    s_nf[0][t] = s_nf[1][t] = s_nf[2][t] = Acc(0);
                 }
             }
+            for (int t = threadIdx.x; t < kHW * 3 * kTile; t += kHT) (&s_nf[0][0][0])[t] = Acc(0);
             __syncthreads();
             const float4 *np = diag ? s_hp : s_np;
             const int *nt = diag ? s_ht : s_nt;
-            Acc(*nf)[kTile] = diag ? s_hf : s_nf;
-
-            // one batch of 32 queued survivors through the force math
-            auto force_batch = [&](int base, int count) {
-                const bool act = lane < count;
-                const uint16_t e = act ? q[base + lane] : 0;
-                const int il = e >> 8, jl = e & 255;
-                const float4 pi = s_hp[il], pj = np[jl];
-                float dx, dy, dz;
-                displacement<MI>(pi, pj, g, a.box, dx, dy, dz);
-                const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                const bool ok = act && (r2 < a.rc2);
-                const float2 ab = s_ab[s_ht[il] * T + nt[jl]];
-                const float kqq = a.kc * pi.w * pj.w;
-                const float ir2 = __frcp_rn(r2);
-                const float ir = rsqrtf(r2);
-                const float ir6 = ir2 * ir2 * ir2;
-                const float ir8 = ir6 * ir2;
-                float f = ab.x * (ir8 * ir6) - ab.y * ir8 + kqq * ir2 * ir;
-                f = ok ? f : 0.0f;
-                const float fx = f * dx, fy = f * dy, fz = f * dz;
-                if (ok) {
-                    if (MODE == MD_ACCUM_FIXED64) {
-                        unsigned long long tx = (unsigned long long)to_fixed(fx, a.status);
-                        unsigned long long ty_ = (unsigned long long)to_fixed(fy, a.status);
-                        unsigned long long tz = (unsigned long long)to_fixed(fz, a.status);
-                        atomicAdd((unsigned long long *)&s_hf[0][il], tx);
-                        atomicAdd((unsigned long long *)&s_hf[1][il], ty_);
-                        atomicAdd((unsigned long long *)&s_hf[2][il], tz);
-                        atomicAdd((unsigned long long *)&nf[0][jl], 0ull - tx);
-                        atomicAdd((unsigned long long *)&nf[1][jl], 0ull - ty_);
-                        atomicAdd((unsigned long long *)&nf[2][jl], 0ull - tz);
-                    } else {
-                        atomicAdd((float *)&s_hf[0][il], fx);
-                        atomicAdd((float *)&s_hf[1][il], fy);
-                        atomicAdd((float *)&s_hf[2][il], fz);
-                        atomicAdd((float *)&nf[0][jl], -fx);
-                        atomicAdd((float *)&nf[1][jl], -fy);
-                        atomicAdd((float *)&nf[2][jl], -fz);
-                    }
-                    cnt += 1;
-                    if (ENERGY) {
-                        e_lj += ab.x * (1.0f / 12.0f) * (ir6 * ir6) - ab.y * (1.0f / 6.0f) * ir6;
-                        e_c += kqq * ir;
-                        vir += f * r2;
-                    }
-                }
-            };
 
             const int nib = mh32 >> 5, njb = mn32 >> 5;
-            const int nitems = diag ? nib * (nib + 1) / 2 : nib * njb;
-            int qn = 0;
-            for (int it = warp; it < nitems; it += kHW) {
-                int ib, jb;
-                if (diag) {
-                    int r = it;
-                    ib = 0;
-                    while (r >= nib - ib) { r -= nib - ib; ++ib; }
-                    jb = ib + r;
-                } else {
-                    ib = it / njb;
-                    jb = it - ib * njb;
-                }
+            for (int ib = warp; ib < nib; ib += kHW) {
                 const int i = ib * 32 + lane;
                 const float4 pi = s_hp[i];
-                unsigned fail = 0u;
+                Acc ax = Acc(0), ay = Acc(0), az = Acc(0);  // i-side sums of this row block
+                for (int jb = diag ? ib : 0; jb < njb; ++jb) {
+                    // ---- filter: bit jj of keep <-> neighbour slot jb*32 + jj
+                    unsigned fail = 0u;
 #pragma unroll 8
-                for (int jj = 0; jj < 32; ++jj) {
-                    const float4 pj = np[jb * 32 + jj];
-                    float s;
-                    if (MI) {
-                        float dx, dy, dz;
-                        displacement<true>(pi, pj, g, a.box, dx, dy, dz);
-                        s = fmaf(-dz, dz, fmaf(-dy, dy, fmaf(-dx, dx, a.rc2m)));
-                    } else {
-                        const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-                        s = fmaf(-dz, dz, fmaf(-dy, dy, fmaf(-dx, dx, a.rc2m)));
+                    for (int jj = 31; jj >= 0; --jj) {
+                        const float4 pj = np[jb * 32 + jj];
+                        float s;
+                        if (MI) {
+                            float dx, dy, dz;
+                            displacement<true>(pi, pj, g, a.box, dx, dy, dz);
+                            s = fmaf(-dz, dz, fmaf(-dy, dy, fmaf(-dx, dx, a.rc2m)));
+                        } else {
+                            const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+                            s = fmaf(-dz, dz, fmaf(-dy, dy, fmaf(-dx, dx, a.rc2m)));
+                        }
+                        // (fail << 1) | sign(s): a negative s rejects the candidate
+                        fail = __funnelshift_l(__float_as_uint(s), fail, 1);
                     }
-                    // (fail << 1) | sign(s): a negative s rejects the candidate
-                    fail = __funnelshift_l(__float_as_uint(s), fail, 1);
-                }
-                // bit b of keep <-> neighbour slot jb*32 + 31 - b
-                unsigned keep = i < mh ? ~fail : 0u;  // padding lanes keep nothing
-                if (diag && ib == jb) keep &= lane == 31 ? 0u : ((1u << (31 - lane)) - 1u);
-                const int c = __popc(keep);
-                int incl = c;
+                    unsigned keep = i < mh ? ~fail : 0u;
+                    if (diag && ib == jb) keep &= ~((2u << lane) - 1u);  // columns above the row
+                    const int c = __popc(keep);
+                    int rs = c;  // inclusive prefix of the row counts
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int v = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= o) incl += v;
-                }
-                const int total = __shfl_sync(0xffffffffu, incl, 31);
-                int pos = qn + incl - c;
-                const uint16_t ibase = (uint16_t)(i << 8);
-                const int jtop = jb * 32 + 31;
-                unsigned m = keep;
-                while (m) {
-                    const int b = __ffs(m) - 1;
-                    m &= m - 1;
-                    q[pos++] = (uint16_t)(ibase | (jtop - b));
-                }
-                __syncwarp();
-                qn += total;
-                int done = 0;
-                while (qn - done >= 32) {
-                    force_batch(done, 32);
-                    done += 32;
-                }
-                if (done > 0) {
-                    const int rem = qn - done;
-                    const uint16_t v = lane < rem ? q[done + lane] : 0;
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int v = __shfl_up_sync(0xffffffffu, rs, o);
+                        if (lane >= o) rs += v;
+                    }
+                    const int total = __shfl_sync(0xffffffffu, rs, 31);
+                    rs -= c;  // exclusive: this row's first entry
+                    if (total == 0) continue;
+                    s_keep[warp][lane] = keep;
+                    s_rs[warp][lane] = rs;
+                    const unsigned col = transpose32(keep, lane);  // column `lane`: rows that keep it
                     __syncwarp();
-                    if (lane < rem) q[lane] = v;
-                    __syncwarp();
-                    qn = rem;
+                    // ---- row passes of at most CAP survivors (one pass unless the item is dense)
+                    for (int r_lo = 0; r_lo < 32;) {
+                        const int base = __shfl_sync(0xffffffffu, rs, r_lo);
+                        const unsigned fit = __ballot_sync(0xffffffffu, lane >= r_lo && rs + c - base <= CAP);
+                        const int r_hi = 32 - __clz(fit);  // rows r_lo .. r_hi-1 (a prefix: rs is monotone)
+                        const int nent = __shfl_sync(0xffffffffu, rs + c, r_hi - 1) - base;
+                        const bool mine = lane >= r_lo && lane < r_hi;
+                        // compaction: each row writes its survivors at its offset
+                        if (mine) {
+                            int pos = rs - base;
+                            unsigned m = keep;
+                            while (m) {
+                                const int b = __ffs(m) - 1;
+                                m &= m - 1;
+                                q[pos++] = (uint16_t)((lane << 5) | b);
+                            }
+                        }
+                        __syncwarp();
+                        // force stage on full warps of survivors
+                        for (int t0 = 0; t0 < nent; t0 += 32) {
+                            const int t = t0 + lane;
+                            const bool act = t < nent;
+                            const uint16_t e = act ? q[t] : 0;
+                            const int il = ib * 32 + (e >> 5), jl = jb * 32 + (e & 31);
+                            const float4 pa = s_hp[il], pb = np[jl];
+                            float dx, dy, dz;
+                            displacement<MI>(pa, pb, g, a.box, dx, dy, dz);
+                            const float r2 = pair_r2(dx, dy, dz);
+                            const bool ok = act && (r2 < a.rc2);
+                            const float2 ab = s_ab[s_ht[il] * T + nt[jl]];
+                            const float kqq = __fmul_rn(a.kc, __fmul_rn(pa.w, pb.w));
+                            float ir, ir2, ir6;
+                            float f = pair_f(r2, ab.x, ab.y, kqq, ir, ir2, ir6);
+                            f = ok ? f : 0.0f;
+                            const float fx = __fmul_rn(f, dx), fy = __fmul_rn(f, dy), fz = __fmul_rn(f, dz);
+                            if (act) {
+                                if (MODE == MD_ACCUM_FIXED64) {
+                                    fb[0][t] = (Acc)(ok ? to_fixed(fx, a.status) : 0);
+                                    fb[1][t] = (Acc)(ok ? to_fixed(fy, a.status) : 0);
+                                    fb[2][t] = (Acc)(ok ? to_fixed(fz, a.status) : 0);
+                                } else {
+                                    fb[0][t] = (Acc)fx;
+                                    fb[1][t] = (Acc)fy;
+                                    fb[2][t] = (Acc)fz;
+                                }
+                            }
+                            if (ok) {
+                                cnt += 1;
+                                if (ENERGY) {
+                                    e_lj += pair_u_lj(ab.x, ab.y, ir6);
+                                    e_c += kqq * ir;
+                                    vir += f * r2;
+                                }
+                            }
+                        }
+                        __syncwarp();
+                        // i-side: the row's survivors are contiguous
+                        if (mine) {
+                            const int p0 = rs - base;
+                            for (int r = 0; r < c; ++r) {
+                                ax += fb[0][p0 + r];
+                                ay += fb[1][p0 + r];
+                                az += fb[2][p0 + r];
+                            }
+                        }
+                        // j-side (Newton's third law): column `lane` gathers its rows' entries
+                        unsigned cm = col & (r_hi == 32 ? ~0u : ((1u << r_hi) - 1u)) & ~((1u << r_lo) - 1u);
+                        Acc sx = Acc(0), sy = Acc(0), sz = Acc(0);
+                        while (cm) {
+                            const int l = __ffs(cm) - 1;
+                            cm &= cm - 1;
+                            const int p = s_rs[warp][l] - base + __popc(s_keep[warp][l] & below);
+                            sx += fb[0][p];
+                            sy += fb[1][p];
+                            sz += fb[2][p];
+                        }
+                        const int jt = jb * 32 + lane;
+                        nfw[0][jt] -= sx;
+                        nfw[1][jt] -= sy;
+                        nfw[2][jt] -= sz;
+                        __syncwarp();
+                        r_lo = r_hi;
+                    }
+                }
+                if (i < mh) {
+                    s_hf[0][i] += ax;
+                    s_hf[1][i] += ay;
+                    s_hf[2][i] += az;
                 }
             }
-            if (qn > 0) force_batch(0, qn);
             __syncthreads();
-            if (!diag) {
-                // reactions on the neighbour tile -> global accumulators
-                for (int t = threadIdx.x; t < mn; t += kHT) {
+            // reactions of this tile: sum the warps' j-side arrays
+            for (int t = threadIdx.x; t < mn; t += kHT) {
+                Acc sx = Acc(0), sy = Acc(0), sz = Acc(0);
+#pragma unroll
+                for (int w = 0; w < kHW; ++w) {
+                    sx += s_nf[w][0][t];
+                    sy += s_nf[w][1][t];
+                    sz += s_nf[w][2][t];
+                }
+                if (diag) {
+                    s_hf[0][t] += sx;
+                    s_hf[1][t] += sy;
+                    s_hf[2][t] += sz;
+                } else {
                     const int s = n_begin + n0 + t;
                     if (MODE == MD_ACCUM_FIXED64) {
                         unsigned long long *acc = static_cast<unsigned long long *>(a.accum);
-                        atomicAdd(&acc[s], (unsigned long long)s_nf[0][t]);
-                        atomicAdd(&acc[(size_t)a.n + s], (unsigned long long)s_nf[1][t]);
-                        atomicAdd(&acc[2 * (size_t)a.n + s], (unsigned long long)s_nf[2][t]);
+                        atomicAdd(&acc[s], (unsigned long long)sx);
+                        atomicAdd(&acc[(size_t)a.n + s], (unsigned long long)sy);
+                        atomicAdd(&acc[2 * (size_t)a.n + s], (unsigned long long)sz);
                     } else {
-                        red_add_v4(static_cast<float4 *>(a.accum) + s, (float)s_nf[0][t],
-                                   (float)s_nf[1][t], (float)s_nf[2][t]);
+                        red_add_v4(static_cast<float4 *>(a.accum) + s, (float)sx, (float)sy, (float)sz);
                     }
                 }
             }
@@ -413,7 +467,15 @@ k_finalize(const void *__restrict__ accum, const int32_t *__restrict__ perm, int
 template <int MODE, bool ENERGY, bool MI>
 void launch_half_t(const HalfArgs &h, dim3 grid, cudaStream_t stream)
 {
-    k_half_shell<MODE, ENERGY, MI><<<grid, kHT, 0, stream>>>(h);
+    using Acc = typename AccT<MODE>::T;
+    const size_t dyn = sizeof(Acc) * kHW * 3 * (kTile + KCap<MODE>::value) +
+                       sizeof(float2) * (size_t)h.ntypes * (size_t)h.ntypes;
+    static const size_t dyn_max = sizeof(Acc) * kHW * 3 * (kTile + KCap<MODE>::value) +
+                                  sizeof(float2) * kMaxTypes * kMaxTypes;
+    static const cudaError_t attr = cudaFuncSetAttribute(
+        k_half_shell<MODE, ENERGY, MI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);
+    (void)attr;
+    k_half_shell<MODE, ENERGY, MI><<<grid, kHT, dyn, stream>>>(h);
 }
 
 }  // namespace

