@@ -121,6 +121,34 @@ int md_build_cells(const float *pos_q, const int32_t *type, int32_t n, const dou
                    void *stream);
 
 /*
+ * md_build_cells_noalloc -- md_build_cells for callers that cannot allocate device memory
+ * (no counterpart in the paper; a convenience of this library).
+ *
+ * Some callers cannot call cudaMalloc, or any routine that allocates, at the point where
+ * they bin atoms: a plugin handed only its input and output buffers by a host program,
+ * code running while other work on the device is being recorded, or an application
+ * whose allocator forbids new allocations inside its step.  This variant takes no
+ * workspace: its scratch lives in one fixed-size device array inside the library, so
+ * the call allocates nothing.  Inputs, outputs, their layouts and the result are those
+ * of md_build_cells (the outputs are bit-identical).
+ *   Limits: n <= MD_NOALLOC_MAX_ATOMS and dims0*dims1*dims2 <= MD_NOALLOC_MAX_CELLS,
+ *   else MD_ERR_TOO_LARGE and nothing is enqueued.  Every GPU that loads the library
+ *   holds MD_NOALLOC_SCRATCH_BYTES for this array until the process exits.
+ *   The first call on each device looks up the array's device address on that device
+ *   (the current one); make that first call before any stream capture begins.
+ *   All calls on a device share the array and it keeps the last call's contents (the
+ *   counters are cleared on every call).  Calls that overlap on the GPU race on it and
+ *   give wrong cell lists: issue them in order on one stream.
+ */
+#define MD_NOALLOC_MAX_ATOMS 131072
+#define MD_NOALLOC_MAX_CELLS 16384
+#define MD_NOALLOC_SCRATCH_BYTES 1114112 /* 2 x 4 B x MAX_ATOMS + 4 B x MAX_CELLS */
+int md_build_cells_noalloc(const float *pos_q, const int32_t *type, int32_t n,
+                           const double *box_L, const int32_t *dims, int32_t *cell_start,
+                           int32_t *perm, float *pos_q_sorted, int32_t *type_sorted,
+                           uint32_t *status, void *stream);
+
+/*
  * md_nonbonded_forces -- short-range non-bonded forces (Eq. 1 + Eq. 2 with the cutoff of
  * Section II.A) over the cell list that md_build_cells produced, in the order of
  * Algorithm 1: each home cell meets its neighbour cells, each candidate pair passes
