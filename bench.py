@@ -38,6 +38,28 @@ FLOP_PER_CANDIDATE = 8
 FLOP_PER_PAIR = 22
 
 
+# DRAM bytes of one md_nonbonded_forces launch (dram__bytes_read.sum + dram__bytes_write.sum
+# of k_half_shell, 92,224-atom lattice) from the ncu capture summarised in
+# profiles/k_half_shell_lattice92k.md, with the SHA-256 of the kernel source it was taken
+# on: the figure is reported as null once that source has changed.
+TRAFFIC_CAPTURE = {"bytes": 3369472, "atoms": 92224,
+                   "kernel_source_sha256": "9d05ca718db861b8029cb1506507be15a7b3aae6a246cc7b0065ee496550de0b"}
+KERNEL_SOURCE = os.path.join(ROOT, "paper_1611_04474_gb300", "csrc", "md_forces_half.cu")
+
+
+def captured_traffic(n_atoms: int):
+    import hashlib
+
+    try:
+        with open(KERNEL_SOURCE, "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+    except OSError:
+        return None
+    if sha != TRAFFIC_CAPTURE["kernel_source_sha256"] or n_atoms != TRAFFIC_CAPTURE["atoms"]:
+        return None
+    return TRAFFIC_CAPTURE["bytes"]
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -137,9 +159,26 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_oracle_rate(s, seconds: float, seed: int = 0):
+def combine_ranks(pairs: float, step_ms: float, e2e_ms: float, device=None):
+    """Whole-job figures over the ranks of a replica run: the pairs all ranks processed,
+    and the slowest rank's device time (max over ranks).  Works on any initialised
+    process group (nccl on GPUs, gloo in the CPU tests)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return pairs, step_ms, e2e_ms
+    t = torch.tensor([step_ms, e2e_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    p = torch.tensor([pairs], dtype=torch.float64, device=device)
+    dist.all_reduce(p, op=dist.ReduceOp.SUM)
+    return float(p[0]), float(t[0]), float(t[1])
+
+
+def cpu_oracle_rate(s, seconds: float, seed: int = 0, gpu_forces=None):
     """The FP64 oracle as it stands, single-threaded, on a sample of the workload's atoms:
-    forces on sampled atoms over the full cell list.  Returns (pairs/s, sample text)."""
+    forces on sampled atoms over the full cell list.  Returns (pairs/s, sample text,
+    accuracy of gpu_forces on the sampled atoms or None)."""
     import oracle
 
     ff = oracle.ForceField.from_system(s)
@@ -149,16 +188,36 @@ def cpu_oracle_rate(s, seconds: float, seed: int = 0):
     done_pairs = 0.0
     t_total = 0.0
     rounds = 0
+    worst_norm, worst_raw, d2, f2 = 0.0, 0.0, 0.0, 0.0
+    skip = np.zeros(s.n, dtype=bool)
+    if gpu_forces is not None:
+        # atoms with a pair whose FP64 r^2 lies within 16 float32 ulps of rc^2 may see that
+        # pair kept by one side and dropped by the other; both are correct roundings, so
+        # those atoms are left out of the error figures (the tests check them separately)
+        ij, _ = oracle.boundary_pairs(p, s.box, s.rc, 16 * 2.0**-24 * s.rc * s.rc)
+        skip[ij.ravel()] = True
     while t_total < seconds:
         sel = rng.choice(s.n, size=sample, replace=False).astype(np.int32)
         t0 = time.perf_counter()
-        _, _, npart = oracle.forces_atoms(p, s.q, s.type, s.box, ff, sel)
+        F, cond, npart = oracle.forces_atoms(p, s.q, s.type, s.box, ff, sel)
         t_total += time.perf_counter() - t0
         done_pairs += float(npart.sum()) / 2.0  # each unique pair is met from both sides
         rounds += 1
+        if gpu_forces is not None:
+            use = ~skip[sel]
+            dF = np.linalg.norm(gpu_forces[sel] - F, axis=1)[use]
+            worst_norm = max(worst_norm, float((dF / cond[use]).max()))
+            worst_raw = max(worst_raw, float((dF / np.linalg.norm(F[use], axis=1)).max()))
+            d2 += float((dF**2).sum())
+            f2 += float((F[use]**2).sum())
+    acc = None
+    if gpu_forces is not None:
+        acc = {"atoms_checked": rounds * sample, "boundary_atoms_excluded": int(skip.sum()),
+               "max_err_over_term_sum": worst_norm, "max_rel_err": worst_raw,
+               "rms_rel_err": (d2 / f2) ** 0.5}
     return done_pairs / t_total, (f"oracle full-shell cell-list forces on {rounds} random samples of "
                                   f"{sample} of the {s.n} atoms ({t_total:.1f} s); unique-pair "
-                                  f"equivalent = partner count / 2")
+                                  f"equivalent = partner count / 2"), acc
 
 
 def run_reference(args):
@@ -169,7 +228,7 @@ def run_reference(args):
     per_step_s = 2.0
     rates = []
     for k in range(args.warmup + args.steps):
-        r, sample = cpu_oracle_rate(s, per_step_s, seed=k)
+        r, sample, _ = cpu_oracle_rate(s, per_step_s, seed=k)
         if k >= args.warmup:
             rates.append(r)
     value = statistics.mean(rates)
@@ -212,6 +271,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     pairs_start = int(eng.pair_count.item())
     candidates = half_shell_candidates(eng.cells.cell_start.cpu().numpy(), eng.dims)
+    forces_start = api.forces_to_f64(eng.forces, mode).cpu().numpy()
 
     # warm-up MD steps
     for _ in range(args.warmup):
@@ -277,17 +337,10 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_ms = [a.elapsed_time(b) for a, b in e2e_ev]
 
-    t_step = sum(step_ms)
     t_force = statistics.mean(force_ms)
-    t_e2e = sum(e2e_ms)
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([t_step, t_e2e], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_step, t_e2e = float(t[0]), float(t[1])
     pairs_per_step = 0.5 * (pairs_start + pairs_end)
-    total_pairs = pairs_per_step * args.steps * world
+    total_pairs, t_step, t_e2e = combine_ranks(pairs_per_step * args.steps, sum(step_ms),
+                                               sum(e2e_ms), device=dev)
     value = total_pairs / (t_step / 1e3)
     e2e_value = total_pairs / (t_e2e / 1e3)
 
@@ -312,7 +365,7 @@ def run_ours(args):
         "candidates_per_eval": candidates,
         "force_kernel_ms": t_force,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                     "frac": achieved / peak_tflops, "traffic": None,
+                     "frac": achieved / peak_tflops, "traffic": captured_traffic(s.n),
                      "kernel": "md_nonbonded_forces",
                      "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz (derived)"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -322,9 +375,11 @@ def run_ours(args):
         "status": status,
     }
     if rank == 0 and not args.no_cpu_baseline:
-        rate, sample = cpu_oracle_rate(s, args.cpu_seconds)
+        rate, sample, acc = cpu_oracle_rate(s, args.cpu_seconds, gpu_forces=forces_start)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": sample}
+        # the same oracle forces also check the GPU's forces of the starting state
+        line["accuracy_vs_oracle"] = acc
     if world > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()

@@ -140,6 +140,26 @@ __device__ __forceinline__ void red_add_v4(float4 *addr, float a, float b, float
                  : "memory");
 }
 
+// Packed FP32 pairs (Blackwell f32x2 ALU ops): two candidates per instruction.
+__device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2_dup(float x)
+{
+    const unsigned long long u = __float_as_uint(x);
+    return u | (u << 32);
+}
+
 struct HalfArgs {
     const int32_t *cell_start;
     const float4 *pq;
@@ -170,30 +190,67 @@ __device__ __forceinline__ unsigned transpose32(unsigned x, int lane)
     return x;
 }
 
+// Bounding box of each 32-atom block of a staged tile (padding slots excluded), one
+// warp per block.  Blocks with no atom get an empty box that is never in range.
+__device__ __forceinline__ void block_boxes(const float (*xyz)[kTile], int m, int m32,
+                                            float (*box)[6])
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int b = warp; b < (m32 >> 5); b += kHW) {
+        const int t = b * 32 + lane;
+        const bool in = t < m;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            float lo = in ? xyz[d][t] : kFar, hi = in ? xyz[d][t] : -kFar;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+                hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+            }
+            if (lane == 0) {
+                box[b][d] = lo;
+                box[b][d + 3] = hi;
+            }
+        }
+    }
+    __syncthreads();
+}
+
 template <int MODE>
 struct KCap {
-    static constexpr int value = MODE == MD_ACCUM_FIXED64 ? 128 : 192;  // survivors buffered per pass
+    static constexpr int value = 128;  // survivors buffered per pass
 };
 
+template <int MODE>
+__device__ __forceinline__ void smem_add(typename AccT<MODE>::T *p, typename AccT<MODE>::T v)
+{
+    if (MODE == MD_ACCUM_FIXED64)
+        atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)v);
+    else
+        atomicAdd(reinterpret_cast<float *>(p), (float)v);
+}
+
 template <int MODE, bool ENERGY, bool MI>
-__global__ void __launch_bounds__(kHT, 6) k_half_shell(HalfArgs a)
+__global__ void __launch_bounds__(kHT, 8) k_half_shell(HalfArgs a)
 {
     using Acc = typename AccT<MODE>::T;
     constexpr int CAP = KCap<MODE>::value;
-    __shared__ float4 s_hp[kTile];
-    __shared__ float4 s_np[kTile];
-    __shared__ int s_ht[kTile];
-    __shared__ int s_nt[kTile];
-    __shared__ Acc s_hf[3][kTile];          // home atoms: i-side sums of the whole cell pair
-    __shared__ uint16_t s_q[kHW][CAP];      // per-warp (row, column) of the buffered pairs
+    __shared__ __align__(16) float s_hxyz[3][kTile];  // home tile (box shift applied)
+    __shared__ __align__(16) float s_nxyz[3][kTile];  // neighbour tile
+    __shared__ float s_hq[kTile], s_nq[kTile];
+    __shared__ int s_ht[kTile], s_nt[kTile];
+    __shared__ float s_hbox[kTile / 32][6];  // per 32-atom block: lo xyz, hi xyz
+    __shared__ float s_nbox[kTile / 32][6];
+    __shared__ Acc s_hf[3][kTile];           // forces on home atoms (whole cell pair)
+    __shared__ Acc s_nf[3][kTile];           // reactions on neighbour atoms (this tile)
+    __shared__ uint16_t s_q[kHW][CAP];       // per-warp (row, column) of buffered pairs
     __shared__ unsigned s_keep[kHW][32];
     __shared__ int s_rs[kHW][32];
-    // dynamic: per-warp j-side sums of the current tile [kHW][3][kTile], per-warp pair
-    // forces of the current item pass [kHW][3][CAP], the LJ table [ntypes * ntypes]
+    // dynamic: per-warp pair forces of the current item pass [kHW][3][CAP], then the LJ
+    // table [ntypes * ntypes]
     extern __shared__ __align__(16) unsigned char s_dyn[];
-    Acc(*s_nf)[3][kTile] = reinterpret_cast<Acc(*)[3][kTile]>(s_dyn);
-    Acc(*s_fb)[3][CAP] = reinterpret_cast<Acc(*)[3][CAP]>(s_dyn + sizeof(Acc) * kHW * 3 * kTile);
-    float2 *s_ab = reinterpret_cast<float2 *>(s_dyn + sizeof(Acc) * kHW * 3 * (kTile + CAP));
+    Acc(*s_fb)[3][CAP] = reinterpret_cast<Acc(*)[3][CAP]>(s_dyn);
+    float2 *s_ab = reinterpret_cast<float2 *>(s_dyn + sizeof(Acc) * kHW * 3 * CAP);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned below = (1u << lane) - 1u;
@@ -216,7 +273,6 @@ __global__ void __launch_bounds__(kHT, 6) k_half_shell(HalfArgs a)
     for (int t = threadIdx.x; t < T * T; t += kHT) s_ab[t] = a.AB[t];
     uint16_t *q = s_q[warp];
     Acc(*fb)[CAP] = s_fb[warp];
-    Acc(*nfw)[kTile] = s_nf[warp];
 
     for (int h0 = 0; h0 < nh; h0 += kTile) {
         const int mh = min(kTile, nh - h0);
@@ -234,16 +290,21 @@ __global__ void __launch_bounds__(kHT, 6) k_half_shell(HalfArgs a)
             } else {
                 p = make_float4(kFar, kFar, kFar, 0.f);
             }
-            s_hp[t] = p;
+            s_hxyz[0][t] = p.x;
+            s_hxyz[1][t] = p.y;
+            s_hxyz[2][t] = p.z;
+            s_hq[t] = p.w;
             s_ht[t] = ty;
             s_hf[0][t] = s_hf[1][t] = s_hf[2][t] = Acc(0);
         }
+        __syncthreads();
+        block_boxes(s_hxyz, mh, mh32, s_hbox);
         for (int n0 = g.self ? h0 : 0; n0 < nn; n0 += kTile) {
             const int mn = min(kTile, nn - n0);
             const bool diag = g.self && n0 == h0;
             const int mn32 = (mn + 31) & ~31;
-            __syncthreads();
             if (!diag) {
+                __syncthreads();
                 for (int t = threadIdx.x; t < mn32; t += kHT) {
                     float4 p;
                     int ty = 0;
@@ -256,167 +317,218 @@ __global__ void __launch_bounds__(kHT, 6) k_half_shell(HalfArgs a)
                     } else {
                         p = make_float4(-kFar, -kFar, -kFar, 0.f);
                     }
-                    s_np[t] = p;
+                    s_nxyz[0][t] = p.x;
+                    s_nxyz[1][t] = p.y;
+                    s_nxyz[2][t] = p.z;
+                    s_nq[t] = p.w;
                     s_nt[t] = ty;
+                    s_nf[0][t] = s_nf[1][t] = s_nf[2][t] = Acc(0);
                 }
+                __syncthreads();
+                block_boxes(s_nxyz, mn, mn32, s_nbox);
             }
-            for (int t = threadIdx.x; t < kHW * 3 * kTile; t += kHT) (&s_nf[0][0][0])[t] = Acc(0);
-            __syncthreads();
-            const float4 *np = diag ? s_hp : s_np;
+            const float(*nxyz)[kTile] = diag ? s_hxyz : s_nxyz;
+            const float *nq = diag ? s_hq : s_nq;
             const int *nt = diag ? s_ht : s_nt;
+            const float(*nbox)[6] = diag ? s_hbox : s_nbox;
+            Acc(*nf)[kTile] = diag ? s_hf : s_nf;
 
             const int nib = mh32 >> 5, njb = mn32 >> 5;
-            for (int ib = warp; ib < nib; ib += kHW) {
+            const int nitems = diag ? nib * (nib + 1) / 2 : nib * njb;
+            int cur_ib = -1;
+            Acc ax = Acc(0), ay = Acc(0), az = Acc(0);  // i-side sums while the row block stays
+            float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
+            unsigned long long xi2 = 0ull, yi2 = 0ull, zi2 = 0ull;
+            const unsigned long long nrc2 = f2_dup(-a.rc2m);
+            for (int it = warp; it < nitems; it += kHW) {
+                int ib, jb;
+                if (diag) {
+                    int r = it;
+                    ib = 0;
+                    while (r >= nib - ib) { r -= nib - ib; ++ib; }
+                    jb = ib + r;
+                } else {
+                    ib = it / njb;
+                    jb = it - ib * njb;
+                }
                 const int i = ib * 32 + lane;
-                const float4 pi = s_hp[i];
-                Acc ax = Acc(0), ay = Acc(0), az = Acc(0);  // i-side sums of this row block
-                for (int jb = diag ? ib : 0; jb < njb; ++jb) {
-                    // ---- filter: bit jj of keep <-> neighbour slot jb*32 + jj
+                if (ib != cur_ib) {
+                    if (cur_ib >= 0 && cur_ib * 32 + lane < mh) {
+                        const int ii = cur_ib * 32 + lane;
+                        smem_add<MODE>(&s_hf[0][ii], ax);
+                        smem_add<MODE>(&s_hf[1][ii], ay);
+                        smem_add<MODE>(&s_hf[2][ii], az);
+                    }
+                    ax = ay = az = Acc(0);
+                    cur_ib = ib;
+                    pi = make_float4(s_hxyz[0][i], s_hxyz[1][i], s_hxyz[2][i], s_hq[i]);
+                    xi2 = f2_dup(pi.x);
+                    yi2 = f2_dup(pi.y);
+                    zi2 = f2_dup(pi.z);
+                }
+                if (!MI) {
+                    // the whole item is out of range if the two blocks' boxes are rc'
+                    // apart (every pair in it would fail the filter)
+                    const float *hb = s_hbox[ib], *nb = nbox[jb];
+                    const float gx = fmaxf(0.f, fmaxf(hb[0] - nb[3], nb[0] - hb[3]));
+                    const float gy = fmaxf(0.f, fmaxf(hb[1] - nb[4], nb[1] - hb[4]));
+                    const float gz = fmaxf(0.f, fmaxf(hb[2] - nb[5], nb[2] - hb[5]));
+                    if (gx * gx + gy * gy + gz * gz >= a.rc2m) continue;
+                }
+                // ---- filter: bit jj of keep <-> neighbour slot jb*32 + jj
+                unsigned keep;
+                if (MI) {
                     unsigned fail = 0u;
 #pragma unroll 8
                     for (int jj = 31; jj >= 0; --jj) {
-                        const float4 pj = np[jb * 32 + jj];
-                        float s;
-                        if (MI) {
-                            float dx, dy, dz;
-                            displacement<true>(pi, pj, g, a.box, dx, dy, dz);
-                            s = fmaf(-dz, dz, fmaf(-dy, dy, fmaf(-dx, dx, a.rc2m)));
-                        } else {
-                            const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-                            s = fmaf(-dz, dz, fmaf(-dy, dy, fmaf(-dx, dx, a.rc2m)));
-                        }
+                        const int jt = jb * 32 + jj;
+                        const float4 pj = make_float4(nxyz[0][jt], nxyz[1][jt], nxyz[2][jt], 0.f);
+                        float dx, dy, dz;
+                        displacement<true>(pi, pj, g, a.box, dx, dy, dz);
+                        const float s = fmaf(-dz, dz, fmaf(-dy, dy, fmaf(-dx, dx, a.rc2m)));
                         // (fail << 1) | sign(s): a negative s rejects the candidate
                         fail = __funnelshift_l(__float_as_uint(s), fail, 1);
                     }
-                    unsigned keep = i < mh ? ~fail : 0u;
-                    if (diag && ib == jb) keep &= ~((2u << lane) - 1u);  // columns above the row
-                    const int c = __popc(keep);
-                    int rs = c;  // inclusive prefix of the row counts
+                    keep = ~fail;
+                } else {
+                    // two candidates per packed instruction; s = r^2 - rc'^2 is negative
+                    // exactly for the candidates to keep
+                    keep = 0u;
+                    const unsigned long long *cx = reinterpret_cast<const unsigned long long *>(&nxyz[0][jb * 32]);
+                    const unsigned long long *cy = reinterpret_cast<const unsigned long long *>(&nxyz[1][jb * 32]);
+                    const unsigned long long *cz = reinterpret_cast<const unsigned long long *>(&nxyz[2][jb * 32]);
+#pragma unroll 4
+                    for (int pp = 15; pp >= 0; --pp) {
+                        const unsigned long long dx = f2_sub(xi2, cx[pp]);
+                        const unsigned long long dy = f2_sub(yi2, cy[pp]);
+                        const unsigned long long dz = f2_sub(zi2, cz[pp]);
+                        unsigned long long s2 = f2_fma(dx, dx, nrc2);
+                        s2 = f2_fma(dy, dy, s2);
+                        s2 = f2_fma(dz, dz, s2);
+                        keep = __funnelshift_l((unsigned)(s2 >> 32), keep, 1);  // slot 2pp+1
+                        keep = __funnelshift_l((unsigned)s2, keep, 1);          // slot 2pp
+                    }
+                }
+                keep = i < mh ? keep : 0u;
+                if (diag && ib == jb) keep &= ~((2u << lane) - 1u);  // columns above the row
+                const int c = __popc(keep);
+                int rs = c;  // inclusive prefix of the row counts
 #pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const int v = __shfl_up_sync(0xffffffffu, rs, o);
-                        if (lane >= o) rs += v;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(0xffffffffu, rs, o);
+                    if (lane >= o) rs += v;
+                }
+                const int total = __shfl_sync(0xffffffffu, rs, 31);
+                rs -= c;  // exclusive: this row's first entry
+                if (total == 0) continue;
+                s_keep[warp][lane] = keep;
+                s_rs[warp][lane] = rs;
+                const unsigned col = transpose32(keep, lane);  // column `lane`: rows that keep it
+                __syncwarp();
+                Acc sx = Acc(0), sy = Acc(0), sz = Acc(0);  // j-side sums of column `lane`
+                // ---- row passes of at most CAP survivors (one pass unless the item is dense)
+                for (int r_lo = 0; r_lo < 32;) {
+                    const int base = __shfl_sync(0xffffffffu, rs, r_lo);
+                    const unsigned fit = __ballot_sync(0xffffffffu, lane >= r_lo && rs + c - base <= CAP);
+                    const int r_hi = 32 - __clz(fit);  // rows r_lo .. r_hi-1 (rs is monotone)
+                    const int nent = __shfl_sync(0xffffffffu, rs + c, r_hi - 1) - base;
+                    const bool mine = lane >= r_lo && lane < r_hi;
+                    // compaction: each row writes its survivors at its offset
+                    if (mine) {
+                        int pos = rs - base;
+                        unsigned m = keep;
+                        while (m) {
+                            const int b = __ffs(m) - 1;
+                            m &= m - 1;
+                            q[pos++] = (uint16_t)((lane << 5) | b);
+                        }
                     }
-                    const int total = __shfl_sync(0xffffffffu, rs, 31);
-                    rs -= c;  // exclusive: this row's first entry
-                    if (total == 0) continue;
-                    s_keep[warp][lane] = keep;
-                    s_rs[warp][lane] = rs;
-                    const unsigned col = transpose32(keep, lane);  // column `lane`: rows that keep it
                     __syncwarp();
-                    // ---- row passes of at most CAP survivors (one pass unless the item is dense)
-                    for (int r_lo = 0; r_lo < 32;) {
-                        const int base = __shfl_sync(0xffffffffu, rs, r_lo);
-                        const unsigned fit = __ballot_sync(0xffffffffu, lane >= r_lo && rs + c - base <= CAP);
-                        const int r_hi = 32 - __clz(fit);  // rows r_lo .. r_hi-1 (a prefix: rs is monotone)
-                        const int nent = __shfl_sync(0xffffffffu, rs + c, r_hi - 1) - base;
-                        const bool mine = lane >= r_lo && lane < r_hi;
-                        // compaction: each row writes its survivors at its offset
-                        if (mine) {
-                            int pos = rs - base;
-                            unsigned m = keep;
-                            while (m) {
-                                const int b = __ffs(m) - 1;
-                                m &= m - 1;
-                                q[pos++] = (uint16_t)((lane << 5) | b);
+                    // force stage on full warps of survivors
+                    for (int t0 = 0; t0 < nent; t0 += 32) {
+                        const int t = t0 + lane;
+                        const bool act = t < nent;
+                        const uint16_t e = act ? q[t] : 0;
+                        const int il = ib * 32 + (e >> 5), jl = jb * 32 + (e & 31);
+                        const float4 pa = make_float4(s_hxyz[0][il], s_hxyz[1][il], s_hxyz[2][il], s_hq[il]);
+                        const float4 pb = make_float4(nxyz[0][jl], nxyz[1][jl], nxyz[2][jl], nq[jl]);
+                        float dx, dy, dz;
+                        displacement<MI>(pa, pb, g, a.box, dx, dy, dz);
+                        const float r2 = pair_r2(dx, dy, dz);
+                        const bool ok = act && (r2 < a.rc2);
+                        const float2 ab = s_ab[s_ht[il] * T + nt[jl]];
+                        const float kqq = __fmul_rn(a.kc, __fmul_rn(pa.w, pb.w));
+                        float ir, ir2, ir6;
+                        float f = pair_f(r2, ab.x, ab.y, kqq, ir, ir2, ir6);
+                        f = ok ? f : 0.0f;
+                        const float fx = __fmul_rn(f, dx), fy = __fmul_rn(f, dy), fz = __fmul_rn(f, dz);
+                        if (act) {
+                            if (MODE == MD_ACCUM_FIXED64) {
+                                fb[0][t] = (Acc)(ok ? to_fixed(fx, a.status) : 0);
+                                fb[1][t] = (Acc)(ok ? to_fixed(fy, a.status) : 0);
+                                fb[2][t] = (Acc)(ok ? to_fixed(fz, a.status) : 0);
+                            } else {
+                                fb[0][t] = (Acc)fx;
+                                fb[1][t] = (Acc)fy;
+                                fb[2][t] = (Acc)fz;
                             }
                         }
-                        __syncwarp();
-                        // force stage on full warps of survivors
-                        for (int t0 = 0; t0 < nent; t0 += 32) {
-                            const int t = t0 + lane;
-                            const bool act = t < nent;
-                            const uint16_t e = act ? q[t] : 0;
-                            const int il = ib * 32 + (e >> 5), jl = jb * 32 + (e & 31);
-                            const float4 pa = s_hp[il], pb = np[jl];
-                            float dx, dy, dz;
-                            displacement<MI>(pa, pb, g, a.box, dx, dy, dz);
-                            const float r2 = pair_r2(dx, dy, dz);
-                            const bool ok = act && (r2 < a.rc2);
-                            const float2 ab = s_ab[s_ht[il] * T + nt[jl]];
-                            const float kqq = __fmul_rn(a.kc, __fmul_rn(pa.w, pb.w));
-                            float ir, ir2, ir6;
-                            float f = pair_f(r2, ab.x, ab.y, kqq, ir, ir2, ir6);
-                            f = ok ? f : 0.0f;
-                            const float fx = __fmul_rn(f, dx), fy = __fmul_rn(f, dy), fz = __fmul_rn(f, dz);
-                            if (act) {
-                                if (MODE == MD_ACCUM_FIXED64) {
-                                    fb[0][t] = (Acc)(ok ? to_fixed(fx, a.status) : 0);
-                                    fb[1][t] = (Acc)(ok ? to_fixed(fy, a.status) : 0);
-                                    fb[2][t] = (Acc)(ok ? to_fixed(fz, a.status) : 0);
-                                } else {
-                                    fb[0][t] = (Acc)fx;
-                                    fb[1][t] = (Acc)fy;
-                                    fb[2][t] = (Acc)fz;
-                                }
-                            }
-                            if (ok) {
-                                cnt += 1;
-                                if (ENERGY) {
-                                    e_lj += pair_u_lj(ab.x, ab.y, ir6);
-                                    e_c += kqq * ir;
-                                    vir += f * r2;
-                                }
+                        if (ok) {
+                            cnt += 1;
+                            if (ENERGY) {
+                                e_lj += pair_u_lj(ab.x, ab.y, ir6);
+                                e_c += kqq * ir;
+                                vir += f * r2;
                             }
                         }
-                        __syncwarp();
-                        // i-side: the row's survivors are contiguous
-                        if (mine) {
-                            const int p0 = rs - base;
-                            for (int r = 0; r < c; ++r) {
-                                ax += fb[0][p0 + r];
-                                ay += fb[1][p0 + r];
-                                az += fb[2][p0 + r];
-                            }
-                        }
-                        // j-side (Newton's third law): column `lane` gathers its rows' entries
-                        unsigned cm = col & (r_hi == 32 ? ~0u : ((1u << r_hi) - 1u)) & ~((1u << r_lo) - 1u);
-                        Acc sx = Acc(0), sy = Acc(0), sz = Acc(0);
-                        while (cm) {
-                            const int l = __ffs(cm) - 1;
-                            cm &= cm - 1;
-                            const int p = s_rs[warp][l] - base + __popc(s_keep[warp][l] & below);
-                            sx += fb[0][p];
-                            sy += fb[1][p];
-                            sz += fb[2][p];
-                        }
-                        const int jt = jb * 32 + lane;
-                        nfw[0][jt] -= sx;
-                        nfw[1][jt] -= sy;
-                        nfw[2][jt] -= sz;
-                        __syncwarp();
-                        r_lo = r_hi;
                     }
+                    __syncwarp();
+                    // i-side: the row's survivors are contiguous
+                    if (mine) {
+                        const int p0 = rs - base;
+                        for (int r = 0; r < c; ++r) {
+                            ax += fb[0][p0 + r];
+                            ay += fb[1][p0 + r];
+                            az += fb[2][p0 + r];
+                        }
+                    }
+                    // j-side (Newton's third law): column `lane` gathers its rows' entries
+                    unsigned cm = col & (r_hi == 32 ? ~0u : ((1u << r_hi) - 1u)) & ~((1u << r_lo) - 1u);
+                    while (cm) {
+                        const int l = __ffs(cm) - 1;
+                        cm &= cm - 1;
+                        const int p = s_rs[warp][l] - base + __popc(s_keep[warp][l] & below);
+                        sx += fb[0][p];
+                        sy += fb[1][p];
+                        sz += fb[2][p];
+                    }
+                    __syncwarp();
+                    r_lo = r_hi;
                 }
-                if (i < mh) {
-                    s_hf[0][i] += ax;
-                    s_hf[1][i] += ay;
-                    s_hf[2][i] += az;
-                }
+                const int jt = jb * 32 + lane;
+                smem_add<MODE>(&nf[0][jt], Acc(0) - sx);
+                smem_add<MODE>(&nf[1][jt], Acc(0) - sy);
+                smem_add<MODE>(&nf[2][jt], Acc(0) - sz);
+            }
+            if (cur_ib >= 0 && cur_ib * 32 + lane < mh) {
+                const int ii = cur_ib * 32 + lane;
+                smem_add<MODE>(&s_hf[0][ii], ax);
+                smem_add<MODE>(&s_hf[1][ii], ay);
+                smem_add<MODE>(&s_hf[2][ii], az);
             }
             __syncthreads();
-            // reactions of this tile: sum the warps' j-side arrays
-            for (int t = threadIdx.x; t < mn; t += kHT) {
-                Acc sx = Acc(0), sy = Acc(0), sz = Acc(0);
-#pragma unroll
-                for (int w = 0; w < kHW; ++w) {
-                    sx += s_nf[w][0][t];
-                    sy += s_nf[w][1][t];
-                    sz += s_nf[w][2][t];
-                }
-                if (diag) {
-                    s_hf[0][t] += sx;
-                    s_hf[1][t] += sy;
-                    s_hf[2][t] += sz;
-                } else {
+            if (!diag) {
+                // reactions of this tile -> global accumulators
+                for (int t = threadIdx.x; t < mn; t += kHT) {
                     const int s = n_begin + n0 + t;
                     if (MODE == MD_ACCUM_FIXED64) {
                         unsigned long long *acc = static_cast<unsigned long long *>(a.accum);
-                        atomicAdd(&acc[s], (unsigned long long)sx);
-                        atomicAdd(&acc[(size_t)a.n + s], (unsigned long long)sy);
-                        atomicAdd(&acc[2 * (size_t)a.n + s], (unsigned long long)sz);
+                        atomicAdd(&acc[s], (unsigned long long)s_nf[0][t]);
+                        atomicAdd(&acc[(size_t)a.n + s], (unsigned long long)s_nf[1][t]);
+                        atomicAdd(&acc[2 * (size_t)a.n + s], (unsigned long long)s_nf[2][t]);
                     } else {
-                        red_add_v4(static_cast<float4 *>(a.accum) + s, (float)sx, (float)sy, (float)sz);
+                        red_add_v4(static_cast<float4 *>(a.accum) + s, (float)s_nf[0][t],
+                                   (float)s_nf[1][t], (float)s_nf[2][t]);
                     }
                 }
             }
@@ -468,9 +580,9 @@ template <int MODE, bool ENERGY, bool MI>
 void launch_half_t(const HalfArgs &h, dim3 grid, cudaStream_t stream)
 {
     using Acc = typename AccT<MODE>::T;
-    const size_t dyn = sizeof(Acc) * kHW * 3 * (kTile + KCap<MODE>::value) +
+    const size_t dyn = sizeof(Acc) * kHW * 3 * KCap<MODE>::value +
                        sizeof(float2) * (size_t)h.ntypes * (size_t)h.ntypes;
-    static const size_t dyn_max = sizeof(Acc) * kHW * 3 * (kTile + KCap<MODE>::value) +
+    static const size_t dyn_max = sizeof(Acc) * kHW * 3 * KCap<MODE>::value +
                                   sizeof(float2) * kMaxTypes * kMaxTypes;
     static const cudaError_t attr = cudaFuncSetAttribute(
         k_half_shell<MODE, ENERGY, MI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);

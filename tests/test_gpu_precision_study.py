@@ -1,0 +1,105 @@
+"""Precision study on the 92,224-atom system (ApoA1 box, rc 12 A), 1,000 NVE steps at 1 fs.
+
+Runs the three accumulation modes side by side:
+  F32      FP32 pair math, FP32 accumulation
+  FIXED64  FP32 pair math, per-pair int64 at 2^-32 (order-independent)
+  F64      FP64 pair math and accumulation (reference mode)
+From the GPU's own state at steps 0, 1, 10, 100 and 1000 the forces are compared with
+the FP64 oracle.  The criterion is the one of tests/parity.py, checked on a sample of
+2,048 atoms for speed, with boundary-pair atoms left out.  FIXED64 is run three times,
+and the SHA-256 of its final positions, velocities and forces must agree.  NVE energy
+drift is reported, not asserted: the paper gives no value for it.
+
+The gentle force field (sigma x 0.5, masses 12-16 amu) keeps the dynamics physical; the
+atoms, charges, box and cutoff are those of the throughput workload.  The report is
+written to gpurun_out/precision_study.json when that folder exists.
+"""
+import hashlib
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1611_04474_gb300 import workloads as W
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+CHECK_STEPS = (0, 1, 10, 100, 1000)
+
+
+def _sha(*arrays):
+    h = hashlib.sha256()
+    for a in arrays:
+        h.update(np.ascontiguousarray(a).tobytes())
+    return h.hexdigest()
+
+
+def _check_forces(api, s, ff, x, F, mode, rng, skip_window):
+    p32 = x.astype(np.float32).astype(np.float64)
+    ij, _ = oracle.boundary_pairs(p32, s.box, s.rc, skip_window)
+    skip = np.zeros(s.n, dtype=bool)
+    skip[ij.ravel()] = True
+    sel = rng.choice(np.nonzero(~skip)[0], size=2048, replace=False).astype(np.int32)
+    Fo, cond, _ = oracle.forces_atoms(p32, s.q, s.type, s.box, ff, sel)
+    Fg = api.forces_to_f64(torch.as_tensor(F), mode).numpy()[sel]
+    dF = np.linalg.norm(Fg - Fo, axis=1)
+    return dict(max_norm=float((dF / cond).max()),
+                max_raw=float((dF / np.linalg.norm(Fo, axis=1)).max()),
+                rms=float(np.sqrt((dF**2).sum() / (Fo**2).sum())))
+
+
+def test_precision_study_92k(cuda_lib):
+    api = cuda_lib
+    s = W.workload_lattice_92k().with_forcefield(0.5, (12.0, 16.0), seed=22)
+    ff = oracle.ForceField.from_system(s)
+    rng = np.random.default_rng(3)
+    window = 16 * 2.0**-24 * s.rc * s.rc
+    report = {"system": "lattice_92224 (sigma x0.5, masses 12-16 amu)", "dt_fs": 1.0,
+              "steps": CHECK_STEPS[-1], "modes": {}}
+    names = {api.ACCUM_F32: "f32", api.ACCUM_FIXED64: "fixed64", api.ACCUM_F64: "f64"}
+    hashes = []
+    for mode in (api.ACCUM_F32, api.ACCUM_FIXED64, api.ACCUM_F64):
+        runs = 3 if mode == api.ACCUM_FIXED64 else 1
+        for run in range(runs):
+            eng = api.Engine(s, mode=mode)
+            log = torch.zeros((CHECK_STEPS[-1], 4), dtype=torch.float64, device="cuda")
+            checks = {}
+            done = 0
+            for k in CHECK_STEPS:
+                if k > done:
+                    eng.step(k - done, dt_fs=1.0, energy_log=log[done:k])
+                    done = k
+                else:
+                    eng.step(0, dt_fs=1.0)  # forces of the start state
+                torch.cuda.synchronize()
+                assert int(eng.status.item()) == 0
+                if run == 0:
+                    checks[k] = _check_forces(api, s, ff, eng.pos.cpu().numpy(),
+                                              eng.forces.cpu().numpy(), mode, rng, window)
+            e = log.cpu().numpy()
+            tot = e[:, 0] + e[:, 1] + e[:, 2]
+            if mode == api.ACCUM_FIXED64:
+                hashes.append(_sha(eng.pos.cpu().numpy(), eng.vel.cpu().numpy(),
+                                   eng.forces.cpu().numpy()))
+            if run == 0:
+                t = np.arange(1, tot.shape[0] + 1, dtype=np.float64)
+                slope = np.polyfit(t, tot, 1)[0]  # kcal/mol per fs
+                report["modes"][names[mode]] = {
+                    "force_checks": checks,
+                    "E_total_start": float(tot[0]), "E_total_end": float(tot[-1]),
+                    "drift_kcal_per_mol_atom_per_ns": float(slope * 1e6 / s.n),
+                    "KE_mean": float(e[:, 2].mean())}
+    report["fixed64_sha256"] = hashes
+    out = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
+    if os.path.isdir(out):
+        with open(os.path.join(out, "precision_study.json"), "w") as f:
+            json.dump(report, f, indent=1)
+    print(json.dumps(report, indent=1))
+    assert len(set(hashes)) == 1, hashes
+    for name, m in report["modes"].items():
+        tol = 1e-12 if name == "f64" else 1e-5
+        for k, c in m["force_checks"].items():
+            assert c["max_norm"] <= tol, (name, k, c)
