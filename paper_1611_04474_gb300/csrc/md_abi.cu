@@ -87,6 +87,7 @@ BoxF make_box(const double *L, const int32_t *dims)
         b.Lhi[d] = (float)L[d];
         b.Llo[d] = (float)(L[d] - (double)b.Lhi[d]);
         b.invL[d] = (float)(1.0 / L[d]);
+        b.inv_edge[d] = (double)dims[d] / L[d];
         b.dims[d] = dims[d];
         prod *= dims[d];
     }

@@ -13,7 +13,8 @@
 namespace mdnb {
 namespace {
 
-constexpr int kIndexThreads = 256;
+constexpr int kIndexThreads = 1024;  // atoms per block of the counting passes
+constexpr int kSmemCells = 8192;     // per-block shared histogram up to this many cells
 constexpr int kScanThreads = 1024;
 constexpr int kSortThreads = 128;
 constexpr int kSortChunk = 2048;  // members staged in shared memory at a time
@@ -23,25 +24,47 @@ __device__ __forceinline__ bool finite3(double x, double y, double z)
     return isfinite(x) && isfinite(y) && isfinite(z);
 }
 
+__device__ __forceinline__ int cell_of(const float4 &p, const BoxF &box, uint32_t *status)
+{
+    double x = p.x, y = p.y, z = p.z;
+    if (!finite3(x, y, z)) {
+        set_status(status, MD_STATUS_NONFINITE);
+        return 0;
+    }
+    int cx = cell_coord(wrap_coord(x, box.L[0]), box.dims[0], box.inv_edge[0]);
+    int cy = cell_coord(wrap_coord(y, box.L[1]), box.dims[1], box.inv_edge[1]);
+    int cz = cell_coord(wrap_coord(z, box.L[2]), box.dims[2], box.inv_edge[2]);
+    return cx + box.dims[0] * (cy + box.dims[1] * cz);
+}
+
+// Per-block histogram in shared memory (grids with up to kSmemCells cells), then one
+// global add per touched cell; larger grids count with warp-aggregated global atomics.
+template <bool SMEM>
 __global__ void __launch_bounds__(kIndexThreads)
 k_cell_index(const float4 *__restrict__ pos_q, int n, BoxF box, int *__restrict__ cell_id,
              int *__restrict__ cell_cnt, uint32_t *status)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    float4 p = pos_q[i];
-    double x = p.x, y = p.y, z = p.z;
-    int c = 0;
-    if (finite3(x, y, z)) {
-        int cx = cell_coord(wrap_coord(x, box.L[0]), box.dims[0], box.L[0]);
-        int cy = cell_coord(wrap_coord(y, box.L[1]), box.dims[1], box.L[1]);
-        int cz = cell_coord(wrap_coord(z, box.L[2]), box.dims[2], box.L[2]);
-        c = cx + box.dims[0] * (cy + box.dims[1] * cz);
-    } else {
-        set_status(status, MD_STATUS_NONFINITE);
+    extern __shared__ int s_hist[];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (SMEM) {
+        for (int t = threadIdx.x; t < box.ncell; t += blockDim.x) s_hist[t] = 0;
+        __syncthreads();
     }
-    cell_id[i] = c;
-    atomicAdd(&cell_cnt[c], 1);
+    int c = -1;
+    if (i < n) {
+        c = cell_of(pos_q[i], box, status);
+        cell_id[i] = c;
+    }
+    if (SMEM) {
+        if (c >= 0) atomicAdd(&s_hist[c], 1);
+        __syncthreads();
+        for (int t = threadIdx.x; t < box.ncell; t += blockDim.x)
+            if (s_hist[t]) atomicAdd(&cell_cnt[t], s_hist[t]);
+    } else {
+        const unsigned act = __ballot_sync(0xffffffffu, c >= 0);
+        const unsigned grp = __match_any_sync(0xffffffffu, c) & act;
+        if (c >= 0 && (threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&cell_cnt[c], __popc(grp));
+    }
 }
 
 // Single block: exclusive scan of the per-cell counts.  Writes cell_start[0..ncell]
@@ -73,17 +96,48 @@ k_scan_cells(int *__restrict__ cnt_cursor, int ncell, int *__restrict__ cell_sta
     if (t == kScanThreads - 1) cell_start[ncell] = sums[t];
 }
 
+// Each atom takes a slot of its cell; the atoms of a warp that share a cell take
+// consecutive slots with one atomic (the order is fixed later by k_cell_sort).
 __global__ void __launch_bounds__(kIndexThreads)
 k_scatter(const int *__restrict__ cell_id, int n, int *__restrict__ cursor, int *__restrict__ perm_tmp)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int slot = atomicAdd(&cursor[cell_id[i]], 1);
-    perm_tmp[slot] = i;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int c = i < n ? cell_id[i] : -1;
+    const unsigned act = __ballot_sync(0xffffffffu, c >= 0);
+    const unsigned grp = __match_any_sync(0xffffffffu, c) & act;
+    const int leader = __ffs(grp) - 1;
+    int base = 0;
+    if (c >= 0 && lane == leader) base = atomicAdd(&cursor[c], __popc(grp));
+    base = __shfl_sync(0xffffffffu, base, leader < 0 ? 0 : leader);
+    if (c >= 0) perm_tmp[base + __popc(grp & ((1u << lane) - 1u))] = i;
 }
 
 // One block per cell.  Members are distinct input indices, so the rank of a member
-// among them (number of smaller members) is its slot in ascending input order.
+// among them (number of smaller members) is its slot in ascending input order.  Each
+// thread ranks one member per round against the whole cell, staged in shared memory
+// (in chunks for cells larger than kSortChunk).
+__device__ __forceinline__ void place(int e, int slot, const float4 *__restrict__ pos_q,
+                                      const int32_t *__restrict__ type, const BoxF &box,
+                                      int32_t *__restrict__ perm, float4 *__restrict__ pos_q_sorted,
+                                      int32_t *__restrict__ type_sorted)
+{
+    perm[slot] = e;
+    const float4 p = pos_q[e];
+    const double x = p.x, y = p.y, z = p.z;
+    float4 o;
+    if (finite3(x, y, z)) {
+        o.x = (float)wrap_coord(x, box.L[0]);
+        o.y = (float)wrap_coord(y, box.L[1]);
+        o.z = (float)wrap_coord(z, box.L[2]);
+    } else {
+        o.x = o.y = o.z = 0.0f;
+    }
+    o.w = p.w;
+    pos_q_sorted[slot] = o;
+    type_sorted[slot] = type[e];
+}
+
 __global__ void __launch_bounds__(kSortThreads)
 k_cell_sort(const int *__restrict__ cell_start, const int *__restrict__ perm_tmp,
             const float4 *__restrict__ pos_q, const int32_t *__restrict__ type, BoxF box,
@@ -91,53 +145,33 @@ k_cell_sort(const int *__restrict__ cell_start, const int *__restrict__ perm_tmp
             int32_t *__restrict__ type_sorted)
 {
     __shared__ int chunk[kSortChunk];
-    int c = blockIdx.x;
-    int s0 = cell_start[c];
-    int m = cell_start[c + 1] - s0;
+    const int c = blockIdx.x;
+    const int s0 = cell_start[c];
+    const int m = cell_start[c + 1] - s0;
     if (m == 0) return;
-    // each thread owns members t, t + blockDim, ...; ranks accumulate chunk by chunk
-    constexpr int kOwn = (kSortChunk + kSortThreads - 1) / kSortThreads;  // when m fits one chunk
-    int own_val[kOwn];
-    int own_rank[kOwn];
-    int rounds = (m + kSortThreads - 1) / kSortThreads;
-    // members beyond kOwn rounds are handled by re-reading perm_tmp (large cells only)
-    for (int base = 0; base < rounds; base += kOwn) {
-        int nr = min(kOwn, rounds - base);
-        for (int r = 0; r < kOwn; ++r) {
-            int t = (base + r) * kSortThreads + threadIdx.x;
-            own_val[r] = (r < nr && t < m) ? perm_tmp[s0 + t] : -1;
-            own_rank[r] = 0;
+    if (m <= kSortChunk) {
+        for (int u = threadIdx.x; u < m; u += kSortThreads) chunk[u] = perm_tmp[s0 + u];
+        __syncthreads();
+        for (int t = threadIdx.x; t < m; t += kSortThreads) {
+            const int e = chunk[t];
+            int rank = 0;
+            for (int u = 0; u < m; ++u) rank += chunk[u] < e;
+            place(e, s0 + rank, pos_q, type, box, perm, pos_q_sorted, type_sorted);
         }
+        return;
+    }
+    for (int base = 0; base < m; base += kSortThreads) {
+        const int t = base + threadIdx.x;
+        const int e = t < m ? perm_tmp[s0 + t] : -1;
+        int rank = 0;
         for (int c0 = 0; c0 < m; c0 += kSortChunk) {
-            int len = min(kSortChunk, m - c0);
+            const int len = min(kSortChunk, m - c0);
             __syncthreads();
             for (int u = threadIdx.x; u < len; u += kSortThreads) chunk[u] = perm_tmp[s0 + c0 + u];
             __syncthreads();
-            for (int u = 0; u < len; ++u) {
-                int v = chunk[u];
-#pragma unroll
-                for (int r = 0; r < kOwn; ++r) own_rank[r] += (v < own_val[r]);
-            }
+            for (int u = 0; u < len; ++u) rank += chunk[u] < e;
         }
-        for (int r = 0; r < kOwn; ++r) {
-            int e = own_val[r];
-            if (e < 0) continue;
-            int slot = s0 + own_rank[r];
-            perm[slot] = e;
-            float4 p = pos_q[e];
-            double x = p.x, y = p.y, z = p.z;
-            float4 o;
-            if (finite3(x, y, z)) {
-                o.x = (float)wrap_coord(x, box.L[0]);
-                o.y = (float)wrap_coord(y, box.L[1]);
-                o.z = (float)wrap_coord(z, box.L[2]);
-            } else {
-                o.x = o.y = o.z = 0.0f;
-            }
-            o.w = p.w;
-            pos_q_sorted[slot] = o;
-            type_sorted[slot] = type[e];
-        }
+        if (e >= 0) place(e, s0 + rank, pos_q, type, box, perm, pos_q_sorted, type_sorted);
     }
 }
 
@@ -155,7 +189,10 @@ cudaError_t launch_build_cells(const float4 *pos_q, const int32_t *type, int n, 
     if (e != cudaSuccess) return e;
     if (n > 0) {
         int g = (n + kIndexThreads - 1) / kIndexThreads;
-        k_cell_index<<<g, kIndexThreads, 0, stream>>>(pos_q, n, box, cell_id, cnt, status);
+        if (box.ncell <= kSmemCells)
+            k_cell_index<true><<<g, kIndexThreads, sizeof(int) * box.ncell, stream>>>(pos_q, n, box, cell_id, cnt, status);
+        else
+            k_cell_index<false><<<g, kIndexThreads, 0, stream>>>(pos_q, n, box, cell_id, cnt, status);
     }
     k_scan_cells<<<1, kScanThreads, 0, stream>>>(cnt, box.ncell, cell_start);
     if (n > 0) {

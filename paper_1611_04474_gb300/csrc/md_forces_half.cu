@@ -218,7 +218,8 @@ __device__ __forceinline__ void block_boxes(const float (*xyz)[kTile], int m, in
 
 template <int MODE>
 struct KCap {
-    static constexpr int value = 128;  // survivors buffered per pass
+    // survivors buffered per pass: one pass holds a typical 32x32 item
+    static constexpr int value = MODE == MD_ACCUM_FIXED64 ? 128 : 256;
 };
 
 template <int MODE>
@@ -244,8 +245,9 @@ __global__ void __launch_bounds__(kHT, 8) k_half_shell(HalfArgs a)
     __shared__ Acc s_hf[3][kTile];           // forces on home atoms (whole cell pair)
     __shared__ Acc s_nf[3][kTile];           // reactions on neighbour atoms (this tile)
     __shared__ uint16_t s_q[kHW][CAP];       // per-warp (row, column) of buffered pairs
-    __shared__ unsigned s_keep[kHW][32];
-    __shared__ int s_rs[kHW][32];
+    __shared__ uint16_t s_cl[kHW][CAP];      // the same pairs in column order: buffer index
+    __shared__ unsigned s_col[kHW][32];      // per-warp column masks (rows keeping column k)
+    __shared__ int s_cs[kHW][32];            // per-warp column offsets within the pass
     // dynamic: per-warp pair forces of the current item pass [kHW][3][CAP], then the LJ
     // table [ntypes * ntypes]
     extern __shared__ __align__(16) unsigned char s_dyn[];
@@ -253,7 +255,6 @@ __global__ void __launch_bounds__(kHT, 8) k_half_shell(HalfArgs a)
     float2 *s_ab = reinterpret_cast<float2 *>(s_dyn + sizeof(Acc) * kHW * 3 * CAP);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const unsigned below = (1u << lane) - 1u;
     const int T = a.ntypes;
     float e_lj = 0.f, e_c = 0.f, vir = 0.f;
     unsigned long long cnt = 0;
@@ -303,9 +304,17 @@ __global__ void __launch_bounds__(kHT, 8) k_half_shell(HalfArgs a)
             const int mn = min(kTile, nn - n0);
             const bool diag = g.self && n0 == h0;
             const int mn32 = (mn + 31) & ~31;
-            if (!diag) {
-                __syncthreads();
-                for (int t = threadIdx.x; t < mn32; t += kHT) {
+            // neighbour tile (for the home cell's own tile: a copy of the home tile, so
+            // that every access below names a fixed shared array)
+            __syncthreads();
+            for (int t = threadIdx.x; t < mn32; t += kHT) {
+                if (diag) {
+                    s_nxyz[0][t] = s_hxyz[0][t];
+                    s_nxyz[1][t] = s_hxyz[1][t];
+                    s_nxyz[2][t] = s_hxyz[2][t];
+                    s_nq[t] = s_hq[t];
+                    s_nt[t] = s_ht[t];
+                } else {
                     float4 p;
                     int ty = 0;
                     if (t < mn) {
@@ -322,16 +331,16 @@ __global__ void __launch_bounds__(kHT, 8) k_half_shell(HalfArgs a)
                     s_nxyz[2][t] = p.z;
                     s_nq[t] = p.w;
                     s_nt[t] = ty;
-                    s_nf[0][t] = s_nf[1][t] = s_nf[2][t] = Acc(0);
                 }
+                s_nf[0][t] = s_nf[1][t] = s_nf[2][t] = Acc(0);
+            }
+            __syncthreads();
+            if (diag) {
+                for (int t = threadIdx.x; t < (mn32 >> 5) * 6; t += kHT) s_nbox[t / 6][t % 6] = s_hbox[t / 6][t % 6];
                 __syncthreads();
+            } else {
                 block_boxes(s_nxyz, mn, mn32, s_nbox);
             }
-            const float(*nxyz)[kTile] = diag ? s_hxyz : s_nxyz;
-            const float *nq = diag ? s_hq : s_nq;
-            const int *nt = diag ? s_ht : s_nt;
-            const float(*nbox)[6] = diag ? s_hbox : s_nbox;
-            Acc(*nf)[kTile] = diag ? s_hf : s_nf;
 
             const int nib = mh32 >> 5, njb = mn32 >> 5;
             const int nitems = diag ? nib * (nib + 1) / 2 : nib * njb;
@@ -369,7 +378,7 @@ __global__ void __launch_bounds__(kHT, 8) k_half_shell(HalfArgs a)
                 if (!MI) {
                     // the whole item is out of range if the two blocks' boxes are rc'
                     // apart (every pair in it would fail the filter)
-                    const float *hb = s_hbox[ib], *nb = nbox[jb];
+                    const float *hb = s_hbox[ib], *nb = s_nbox[jb];
                     const float gx = fmaxf(0.f, fmaxf(hb[0] - nb[3], nb[0] - hb[3]));
                     const float gy = fmaxf(0.f, fmaxf(hb[1] - nb[4], nb[1] - hb[4]));
                     const float gz = fmaxf(0.f, fmaxf(hb[2] - nb[5], nb[2] - hb[5]));
@@ -382,7 +391,7 @@ __global__ void __launch_bounds__(kHT, 8) k_half_shell(HalfArgs a)
 #pragma unroll 8
                     for (int jj = 31; jj >= 0; --jj) {
                         const int jt = jb * 32 + jj;
-                        const float4 pj = make_float4(nxyz[0][jt], nxyz[1][jt], nxyz[2][jt], 0.f);
+                        const float4 pj = make_float4(s_nxyz[0][jt], s_nxyz[1][jt], s_nxyz[2][jt], 0.f);
                         float dx, dy, dz;
                         displacement<true>(pi, pj, g, a.box, dx, dy, dz);
                         const float s = fmaf(-dz, dz, fmaf(-dy, dy, fmaf(-dx, dx, a.rc2m)));
@@ -394,9 +403,9 @@ __global__ void __launch_bounds__(kHT, 8) k_half_shell(HalfArgs a)
                     // two candidates per packed instruction; s = r^2 - rc'^2 is negative
                     // exactly for the candidates to keep
                     keep = 0u;
-                    const unsigned long long *cx = reinterpret_cast<const unsigned long long *>(&nxyz[0][jb * 32]);
-                    const unsigned long long *cy = reinterpret_cast<const unsigned long long *>(&nxyz[1][jb * 32]);
-                    const unsigned long long *cz = reinterpret_cast<const unsigned long long *>(&nxyz[2][jb * 32]);
+                    const unsigned long long *cx = reinterpret_cast<const unsigned long long *>(&s_nxyz[0][jb * 32]);
+                    const unsigned long long *cy = reinterpret_cast<const unsigned long long *>(&s_nxyz[1][jb * 32]);
+                    const unsigned long long *cz = reinterpret_cast<const unsigned long long *>(&s_nxyz[2][jb * 32]);
 #pragma unroll 4
                     for (int pp = 15; pp >= 0; --pp) {
                         const unsigned long long dx = f2_sub(xi2, cx[pp]);
@@ -421,10 +430,8 @@ __global__ void __launch_bounds__(kHT, 8) k_half_shell(HalfArgs a)
                 const int total = __shfl_sync(0xffffffffu, rs, 31);
                 rs -= c;  // exclusive: this row's first entry
                 if (total == 0) continue;
-                s_keep[warp][lane] = keep;
-                s_rs[warp][lane] = rs;
                 const unsigned col = transpose32(keep, lane);  // column `lane`: rows that keep it
-                __syncwarp();
+                uint16_t *cl = s_cl[warp];
                 Acc sx = Acc(0), sy = Acc(0), sz = Acc(0);  // j-side sums of column `lane`
                 // ---- row passes of at most CAP survivors (one pass unless the item is dense)
                 for (int r_lo = 0; r_lo < 32;) {
@@ -433,6 +440,20 @@ __global__ void __launch_bounds__(kHT, 8) k_half_shell(HalfArgs a)
                     const int r_hi = 32 - __clz(fit);  // rows r_lo .. r_hi-1 (rs is monotone)
                     const int nent = __shfl_sync(0xffffffffu, rs + c, r_hi - 1) - base;
                     const bool mine = lane >= r_lo && lane < r_hi;
+                    // column `lane` restricted to the pass's rows, and its offset in
+                    // column order
+                    const unsigned prow = (r_hi == 32 ? ~0u : ((1u << r_hi) - 1u)) & ~((1u << r_lo) - 1u);
+                    const unsigned cm = col & prow;
+                    const int cc = __popc(cm);
+                    int cs = cc;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int v = __shfl_up_sync(0xffffffffu, cs, o);
+                        if (lane >= o) cs += v;
+                    }
+                    cs -= cc;
+                    s_col[warp][lane] = cm;
+                    s_cs[warp][lane] = cs;
                     // compaction: each row writes its survivors at its offset
                     if (mine) {
                         int pos = rs - base;
@@ -451,18 +472,22 @@ __global__ void __launch_bounds__(kHT, 8) k_half_shell(HalfArgs a)
                         const uint16_t e = act ? q[t] : 0;
                         const int il = ib * 32 + (e >> 5), jl = jb * 32 + (e & 31);
                         const float4 pa = make_float4(s_hxyz[0][il], s_hxyz[1][il], s_hxyz[2][il], s_hq[il]);
-                        const float4 pb = make_float4(nxyz[0][jl], nxyz[1][jl], nxyz[2][jl], nq[jl]);
+                        const float4 pb = make_float4(s_nxyz[0][jl], s_nxyz[1][jl], s_nxyz[2][jl], s_nq[jl]);
                         float dx, dy, dz;
                         displacement<MI>(pa, pb, g, a.box, dx, dy, dz);
                         const float r2 = pair_r2(dx, dy, dz);
                         const bool ok = act && (r2 < a.rc2);
-                        const float2 ab = s_ab[s_ht[il] * T + nt[jl]];
+                        const float2 ab = s_ab[s_ht[il] * T + s_nt[jl]];
                         const float kqq = __fmul_rn(a.kc, __fmul_rn(pa.w, pb.w));
                         float ir, ir2, ir6;
                         float f = pair_f(r2, ab.x, ab.y, kqq, ir, ir2, ir6);
                         f = ok ? f : 0.0f;
                         const float fx = __fmul_rn(f, dx), fy = __fmul_rn(f, dy), fz = __fmul_rn(f, dz);
                         if (act) {
+                            // this pair's place in column order: column offset + rank of
+                            // its row among the column's rows
+                            const int k = e & 31, l = e >> 5;
+                            cl[s_cs[warp][k] + __popc(s_col[warp][k] & ((1u << l) - 1u))] = (uint16_t)t;
                             if (MODE == MD_ACCUM_FIXED64) {
                                 fb[0][t] = (Acc)(ok ? to_fixed(fx, a.status) : 0);
                                 fb[1][t] = (Acc)(ok ? to_fixed(fy, a.status) : 0);
@@ -492,12 +517,10 @@ __global__ void __launch_bounds__(kHT, 8) k_half_shell(HalfArgs a)
                             az += fb[2][p0 + r];
                         }
                     }
-                    // j-side (Newton's third law): column `lane` gathers its rows' entries
-                    unsigned cm = col & (r_hi == 32 ? ~0u : ((1u << r_hi) - 1u)) & ~((1u << r_lo) - 1u);
-                    while (cm) {
-                        const int l = __ffs(cm) - 1;
-                        cm &= cm - 1;
-                        const int p = s_rs[warp][l] - base + __popc(s_keep[warp][l] & below);
+                    // j-side (Newton's third law): column `lane` sums its entries, listed
+                    // contiguously in column order
+                    for (int r = 0; r < cc; ++r) {
+                        const int p = cl[cs + r];
                         sx += fb[0][p];
                         sy += fb[1][p];
                         sz += fb[2][p];
@@ -506,9 +529,9 @@ __global__ void __launch_bounds__(kHT, 8) k_half_shell(HalfArgs a)
                     r_lo = r_hi;
                 }
                 const int jt = jb * 32 + lane;
-                smem_add<MODE>(&nf[0][jt], Acc(0) - sx);
-                smem_add<MODE>(&nf[1][jt], Acc(0) - sy);
-                smem_add<MODE>(&nf[2][jt], Acc(0) - sz);
+                smem_add<MODE>(&s_nf[0][jt], Acc(0) - sx);
+                smem_add<MODE>(&s_nf[1][jt], Acc(0) - sy);
+                smem_add<MODE>(&s_nf[2][jt], Acc(0) - sz);
             }
             if (cur_ib >= 0 && cur_ib * 32 + lane < mh) {
                 const int ii = cur_ib * 32 + lane;
@@ -517,7 +540,14 @@ __global__ void __launch_bounds__(kHT, 8) k_half_shell(HalfArgs a)
                 smem_add<MODE>(&s_hf[2][ii], az);
             }
             __syncthreads();
-            if (!diag) {
+            if (diag) {
+                // the neighbour tile is the home tile: reactions join the home sums
+                for (int t = threadIdx.x; t < mn; t += kHT) {
+                    s_hf[0][t] += s_nf[0][t];
+                    s_hf[1][t] += s_nf[1][t];
+                    s_hf[2][t] += s_nf[2][t];
+                }
+            } else {
                 // reactions of this tile -> global accumulators
                 for (int t = threadIdx.x; t < mn; t += kHT) {
                     const int s = n_begin + n0 + t;

@@ -30,6 +30,7 @@ struct BoxF {
     float Lhi[3];   // float(L): the leading part of L
     float Llo[3];   // float(L - Lhi): the remainder, so Lhi + Llo == L to ~2^-48 L
     float invL[3];  // 1/L rounded to float
+    double inv_edge[3];  // dims / L (one IEEE division, the same bits on host and device)
     int dims[3];
     int ncell;
 };
@@ -57,19 +58,22 @@ __device__ __forceinline__ void set_status(uint32_t *status, uint32_t bits)
     if (status) atomicOr(status, bits);
 }
 
-// Wrap a coordinate into [0, L) in FP64 (the documented rule).
+// Wrap a coordinate into [0, L) in FP64 (the documented rule).  A coordinate already
+// in [0, L) is returned as it is, which is what the rule gives for it (even when x/L
+// rounds up to 1, the fold-back restores x exactly), without the FP64 division.
 __device__ __forceinline__ double wrap_coord(double x, double L)
 {
+    if (x >= 0.0 && x < L) return x;
     double w = x - L * floor(x / L);
     if (w < 0.0) w += L;
     if (w >= L) w -= L;
     return w;
 }
 
-// Cell index along one axis of a wrapped coordinate: floor(w * (n/L)) clamped.
-__device__ __forceinline__ int cell_coord(double w, int nc, double L)
+// Cell index along one axis of a wrapped coordinate: floor(w * (n/L)) clamped, with
+// inv_edge = n/L from the host.
+__device__ __forceinline__ int cell_coord(double w, int nc, double inv_edge)
 {
-    double inv_edge = (double)nc / L;
     double f = floor(w * inv_edge);
     return f < 0.0 ? 0 : (f > (double)(nc - 1) ? nc - 1 : (int)f);
 }
@@ -101,13 +105,23 @@ __device__ __forceinline__ float pair_r2(float dx, float dy, float dz)
     return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
 }
 
+// 1/sqrt(x) from the hardware approximation (MUFU, ~2^-22 relative) refined by one
+// Newton-Raphson step y' = y (3 - x y^2) / 2, which leaves about one ulp.
+__device__ __forceinline__ float rsqrt_nr(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    const float h = __fmul_rn(0.5f, x);
+    return __fmul_rn(y, __fmaf_rn(-h, __fmul_rn(y, y), 1.5f));
+}
+
 // Scalar f of F = f * r (Eq. 1: A/r^14 - B/r^8, Eq. 2: k q1 q2 / r^3); also returns
 // 1/r, 1/r^2, 1/r^6 for the energies.
 __device__ __forceinline__ float pair_f(float r2, float A, float B, float kqq, float &ir,
                                         float &ir2, float &ir6)
 {
-    ir2 = __frcp_rn(r2);
-    ir = rsqrtf(r2);
+    ir = rsqrt_nr(r2);
+    ir2 = __fmul_rn(ir, ir);
     ir6 = __fmul_rn(__fmul_rn(ir2, ir2), ir2);
     const float ir8 = __fmul_rn(ir6, ir2);
     const float lj = __fmaf_rn(A, __fmul_rn(ir8, ir6), -__fmul_rn(B, ir8));
