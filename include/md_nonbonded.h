@@ -203,6 +203,44 @@ int md_step(double *pos, double *vel, void *forces, int32_t forces_valid, const 
             double *energy_log, void *workspace, size_t ws_bytes, uint32_t *status,
             void *stream);
 
+/*
+ * Batches of independent systems (many small MD problems advanced together; the
+ * paper's method applied to each system independently).
+ *
+ * The systems are stored back to back: system s owns atoms off[s] .. off[s+1]-1 of
+ * every per-atom array, off[0] = 0, off[s+1] = off[s] + systems[s].n.  Each system has
+ * its own box, cutoff and force field and obeys the rules of md_cell_dims.  Cells of
+ * all systems are numbered globally and each launch covers every system: one kernel
+ * grid for the systems with >= 3 cells per axis, one for those with an axis of 2.
+ */
+typedef struct md_system_desc {
+    int32_t n;        /* atoms of this system */
+    int32_t reserved; /* set to 0 */
+    double box_L[3];
+    md_forcefield ff; /* ff.AB is a DEVICE pointer; may be shared between systems */
+} md_system_desc;
+
+/* Workspace bytes for a batch (0 on invalid systems). */
+size_t md_batch_workspace_bytes(int32_t nsys, const md_system_desc *systems);
+
+/* Writes the batch's per-system descriptors into the workspace (host -> device copies,
+ * then waits for them).  Call once per batch before md_batch_step, and again whenever
+ * the systems change; the workspace must stay with this batch. */
+int md_batch_prepare(int32_t nsys, const md_system_desc *systems, void *workspace,
+                     size_t ws_bytes, void *stream);
+
+/* md_step for a batch prepared in `workspace` with the same `systems` (host).  Arrays
+ * are the concatenations described above; mode MD_ACCUM_F32 or MD_ACCUM_FIXED64.
+ * pair_count: device uint64[nsys] or NULL; the unique within-cutoff pairs of every
+ * force evaluation are added to it (the caller zeroes it).  Makes no host<->device
+ * copies and no allocation, so a sequence of calls can be captured in a CUDA graph
+ * (after one call outside the capture). */
+int md_batch_step(int32_t nsys, const md_system_desc *systems, double *pos, double *vel,
+                  void *forces, int32_t forces_valid, const float *inv_mass, const float *q,
+                  const int32_t *type, int32_t mode, double dt_fs, int32_t n_steps,
+                  unsigned long long *pair_count, void *workspace, size_t ws_bytes,
+                  uint32_t *status, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

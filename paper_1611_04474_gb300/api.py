@@ -29,7 +29,8 @@ STATUS_BAD_TYPE = 4
 FIXED_SCALE = 2.0**32
 
 EXPORTS = ("md_strerror", "md_abi_version", "md_cell_dims", "md_workspace_bytes", "md_build_cells",
-           "md_nonbonded_forces", "md_nonbonded_forces_algo", "md_step")
+           "md_build_cells_noalloc", "md_nonbonded_forces", "md_nonbonded_forces_algo", "md_step",
+           "md_batch_workspace_bytes", "md_batch_prepare", "md_batch_step")
 
 _lib = None
 
@@ -43,6 +44,11 @@ class MDError(RuntimeError):
 class md_forcefield(ctypes.Structure):
     _fields_ = [("ntypes", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("AB", ctypes.c_void_p), ("k_coulomb", ctypes.c_double), ("rc", ctypes.c_double)]
+
+
+class md_system_desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("box_L", ctypes.c_double * 3), ("ff", md_forcefield)]
 
 
 def load(path: str | None = None):
@@ -73,6 +79,12 @@ def load(path: str | None = None):
     lib.md_nonbonded_forces_algo.restype = ctypes.c_int
     lib.md_step.argtypes = [P, P, P, i32, P, P, P, i32, P, P, i32, f64, i32, P, P, sz, P, P]
     lib.md_step.restype = ctypes.c_int
+    lib.md_batch_workspace_bytes.argtypes = [i32, P]
+    lib.md_batch_workspace_bytes.restype = sz
+    lib.md_batch_prepare.argtypes = [i32, P, P, sz, P]
+    lib.md_batch_prepare.restype = ctypes.c_int
+    lib.md_batch_step.argtypes = [i32, P, P, P, P, i32, P, P, P, i32, f64, i32, P, P, sz, P, P]
+    lib.md_batch_step.restype = ctypes.c_int
     del V
     if path is None:
         _lib = lib
@@ -283,3 +295,54 @@ class Engine:
              self.types, self.box, self.ff, self.mode, dt_fs, n_steps, self.workspace,
              energy_log=energy_log, status=self.status, stream=stream)
         self.forces_valid = True
+
+
+class Batch:
+    """Independent systems advanced together (md_batch_*): the systems' arrays are
+    concatenated on the device once; every step is one set of launches for all of them."""
+
+    def __init__(self, systems, mode=ACCUM_FIXED64, device="cuda"):
+        if mode not in (ACCUM_F32, ACCUM_FIXED64):
+            raise ValueError("batched mode must be ACCUM_F32 or ACCUM_FIXED64")
+        self.systems = list(systems)
+        self.mode = mode
+        self.nsys = len(self.systems)
+        self.ffs = [ForceField.from_system(s, device) for s in self.systems]
+        self.desc = (md_system_desc * self.nsys)()
+        for k, (s, ff) in enumerate(zip(self.systems, self.ffs)):
+            self.desc[k].n = s.n
+            self.desc[k].reserved = 0
+            for d in range(3):
+                self.desc[k].box_L[d] = float(s.box[d])
+            self.desc[k].ff = ff._c
+        self.offsets = np.concatenate([[0], np.cumsum([s.n for s in self.systems])]).astype(np.int64)
+        self.n = int(self.offsets[-1])
+        cat = lambda f, dt: torch.as_tensor(np.concatenate([f(s) for s in self.systems]).astype(dt)).to(device)
+        self.pos = cat(lambda s: s.pos.astype(np.float64), np.float64).contiguous()
+        self.vel = cat(lambda s: s.vel, np.float64).contiguous()
+        self.q = cat(lambda s: s.q, np.float32)
+        self.types = cat(lambda s: s.type, np.int32)
+        self.inv_mass = cat(lambda s: s.inv_mass, np.float32)
+        self.forces = torch.zeros((self.n, 3), dtype=FORCE_DTYPE[mode], device=device)
+        self.pair_count = torch.zeros(self.nsys, dtype=torch.int64, device=device)
+        self.status = torch.zeros(1, dtype=torch.int32, device=device)
+        nbytes = int(load().md_batch_workspace_bytes(self.nsys, ctypes.byref(self.desc)))
+        if nbytes == 0:
+            raise ValueError("invalid batch (a cutoff at or above L/2, bad n or force field)")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        self.forces_valid = False
+        _check("md_batch_prepare", load().md_batch_prepare(
+            self.nsys, ctypes.byref(self.desc), _ptr(self.workspace), nbytes,
+            _stream(None)))
+
+    def step(self, n_steps=1, dt_fs=1.0, count_pairs=False, stream=None):
+        _check("md_batch_step", load().md_batch_step(
+            self.nsys, ctypes.byref(self.desc), _ptr(self.pos), _ptr(self.vel), _ptr(self.forces),
+            int(self.forces_valid), _ptr(self.inv_mass), _ptr(self.q), _ptr(self.types),
+            int(self.mode), float(dt_fs), int(n_steps),
+            _ptr(self.pair_count) if count_pairs else None, _ptr(self.workspace),
+            self.workspace.numel(), _ptr(self.status), _stream(stream)))
+        self.forces_valid = True
+
+    def system_slice(self, k):
+        return slice(int(self.offsets[k]), int(self.offsets[k + 1]))

@@ -4,6 +4,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <vector>
+
 #include "md_internal.cuh"
 
 namespace mdnb {
@@ -119,6 +121,42 @@ WsLayout ws_layout(int n, int ncell)
     w.st_pos_q = off;        off = align_up(off + sizeof(float4) * nn);
     w.total = off;
     return w;
+}
+
+// Batch layout on the host: per-system cells and the scratch of the whole batch.
+static int batch_layout(int32_t nsys, const md_system_desc *systems, BatchLayout *bl,
+                        std::vector<int32_t> *dims_out)
+{
+    if (nsys < 1 || !systems) return MD_ERR_INVALID_ARG;
+    long long n = 0, ncell = 0, ncell_mi = 0;
+    dims_out->resize(3 * (size_t)nsys);
+    for (int s = 0; s < nsys; ++s) {
+        const md_system_desc &d = systems[s];
+        if (d.n < 0) return MD_ERR_INVALID_ARG;
+        int e = check_ff(&d.ff);
+        if (e) return e;
+        int32_t *dims = dims_out->data() + 3 * s;
+        if ((e = compute_dims(d.box_L, d.ff.rc, dims))) return e;
+        long long nc = (long long)dims[0] * dims[1] * dims[2];
+        n += d.n;
+        ncell += nc;
+        if (dims[0] < 3 || dims[1] < 3 || dims[2] < 3) ncell_mi += nc;
+    }
+    if (n > kMaxAtoms || ncell > kMaxCells) return MD_ERR_TOO_LARGE;
+    bl->nsys = nsys;
+    bl->n = (int)n;
+    bl->ncell = (int)ncell;
+    bl->ncell_mi = (int)ncell_mi;
+    bl->ncell_reg = (int)(ncell - ncell_mi);
+    size_t off = 0;
+    bl->sys = off;       off = align_up(off + sizeof(SysDesc) * (size_t)nsys);
+    bl->cell_sys = off;  off = align_up(off + sizeof(int) * (size_t)ncell);
+    bl->cell_list = off; off = align_up(off + sizeof(int) * (size_t)ncell);
+    bl->atom_sys = off;  off = align_up(off + sizeof(int) * (size_t)(n > 0 ? n : 1));
+    bl->run = ws_layout((int)n, (int)ncell);
+    bl->run_base = off;
+    bl->total = off + bl->run.total;
+    return MD_OK;
 }
 
 }  // namespace mdnb
@@ -305,6 +343,134 @@ int md_step(double *pos, double *vel, void *forces, int32_t forces_valid, const 
             ce = launch_energy_log_row(vel, inv_mass, n, ev, energy_log + 4 * (size_t)st, ws, wsp, s);
             if (ce != cudaSuccess) return MD_ERR_CUDA;
         }
+    }
+    return MD_OK;
+}
+
+size_t md_batch_workspace_bytes(int32_t nsys, const md_system_desc *systems)
+{
+    BatchLayout bl;
+    std::vector<int32_t> dims;
+    if (batch_layout(nsys, systems, &bl, &dims) != MD_OK) return 0;
+    return bl.total + kAlign;
+}
+
+int md_batch_prepare(int32_t nsys, const md_system_desc *systems, void *workspace, size_t ws_bytes,
+                     void *stream)
+{
+    BatchLayout bl;
+    std::vector<int32_t> dims;
+    int e = batch_layout(nsys, systems, &bl, &dims);
+    if (e) return e;
+    if (!workspace) return MD_ERR_WORKSPACE;
+    uintptr_t p = reinterpret_cast<uintptr_t>(workspace);
+    uintptr_t a = (p + kAlign - 1) & ~(uintptr_t)(kAlign - 1);
+    if (ws_bytes < (a - p) + bl.total) return MD_ERR_WORKSPACE;
+    char *wsp = reinterpret_cast<char *>(a);
+    std::vector<SysDesc> sys((size_t)nsys);
+    std::vector<int> cell_sys((size_t)bl.ncell), cell_list((size_t)bl.ncell), atom_sys((size_t)bl.n);
+    int atom = 0, cell = 0, reg = 0, mi = bl.ncell_reg;
+    for (int s = 0; s < nsys; ++s) {
+        const md_system_desc &d = systems[s];
+        SysDesc &o = sys[s];
+        o.box = make_box(d.box_L, dims.data() + 3 * s);
+        o.AB = reinterpret_cast<const float2 *>(d.ff.AB);
+        o.ntypes = d.ff.ntypes;
+        o.kc = (float)d.ff.k_coulomb;
+        o.kc64 = d.ff.k_coulomb;
+        o.mi = half_shell_pairs_per_cell(o.box) == 27;
+        cutoff_thresholds(o.box, d.ff.rc, o.mi != 0, &o.rc2, &o.rc2m);
+        o.atom_offset = atom;
+        o.natoms = d.n;
+        o.cell_offset = cell;
+        for (int c = 0; c < o.box.ncell; ++c) {
+            cell_sys[(size_t)cell + c] = s;
+            cell_list[(size_t)(o.mi ? mi++ : reg++)] = cell + c;
+        }
+        for (int i = 0; i < d.n; ++i) atom_sys[(size_t)atom + i] = s;
+        atom += d.n;
+        cell += o.box.ncell;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t ce = cudaMemcpyAsync(wsp + bl.sys, sys.data(), sizeof(SysDesc) * sys.size(),
+                                     cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(wsp + bl.cell_sys, cell_sys.data(), sizeof(int) * cell_sys.size(),
+                             cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(wsp + bl.cell_list, cell_list.data(), sizeof(int) * cell_list.size(),
+                             cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess && bl.n > 0)
+        ce = cudaMemcpyAsync(wsp + bl.atom_sys, atom_sys.data(), sizeof(int) * atom_sys.size(),
+                             cudaMemcpyHostToDevice, st);
+    // the host vectors are released on return: wait for the copies to finish reading them
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    return ce == cudaSuccess ? MD_OK : MD_ERR_CUDA;
+}
+
+int md_batch_step(int32_t nsys, const md_system_desc *systems, double *pos, double *vel,
+                  void *forces, int32_t forces_valid, const float *inv_mass, const float *q,
+                  const int32_t *type, int32_t mode, double dt_fs, int32_t n_steps,
+                  unsigned long long *pair_count, void *workspace, size_t ws_bytes,
+                  uint32_t *status, void *stream)
+{
+    BatchLayout bl;
+    std::vector<int32_t> dims;
+    int e = batch_layout(nsys, systems, &bl, &dims);
+    if (e) return e;
+    if (n_steps < 0 || !(dt_fs > 0.0) || !isfinite(dt_fs)) return MD_ERR_INVALID_ARG;
+    if (mode != MD_ACCUM_F32 && mode != MD_ACCUM_FIXED64) return MD_ERR_INVALID_ARG;
+    if (bl.n > 0 && (!pos || !vel || !forces || !inv_mass || !q || !type)) return MD_ERR_INVALID_ARG;
+    if (!workspace) return MD_ERR_WORKSPACE;
+    uintptr_t p = reinterpret_cast<uintptr_t>(workspace);
+    uintptr_t al = (p + kAlign - 1) & ~(uintptr_t)(kAlign - 1);
+    if (ws_bytes < (al - p) + bl.total) return MD_ERR_WORKSPACE;
+    char *wsp = reinterpret_cast<char *>(al);
+    if (bl.n == 0 || (n_steps == 0 && forces_valid)) return MD_OK;
+    BatchArgs b;
+    b.sys = reinterpret_cast<const SysDesc *>(wsp + bl.sys);
+    b.cell_sys = reinterpret_cast<const int *>(wsp + bl.cell_sys);
+    b.cell_list = reinterpret_cast<const int *>(wsp + bl.cell_list);
+    b.atom_sys = reinterpret_cast<const int *>(wsp + bl.atom_sys);
+    b.nsys = bl.nsys;
+    b.n = bl.n;
+    b.ncell = bl.ncell;
+    b.ncell_mi = bl.ncell_mi;
+    b.ncell_reg = bl.ncell_reg;
+    b.max_ntypes = 0;
+    for (int k = 0; k < nsys; ++k) b.max_ntypes = systems[k].ff.ntypes > b.max_ntypes ? systems[k].ff.ntypes : b.max_ntypes;
+    char *run = wsp + bl.run_base;
+    const WsLayout &ws = bl.run;
+    int32_t *cs = reinterpret_cast<int32_t *>(run + ws.st_cell_start);
+    int32_t *pm = reinterpret_cast<int32_t *>(run + ws.st_perm);
+    float4 *pqs = reinterpret_cast<float4 *>(run + ws.st_pos_q_sorted);
+    int32_t *tys = reinterpret_cast<int32_t *>(run + ws.st_type_sorted);
+    float4 *pq = reinterpret_cast<float4 *>(run + ws.st_pos_q);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    ForceArgs a = {};
+    a.cell_start = cs;
+    a.perm = pm;
+    a.pos_q_sorted = pqs;
+    a.type_sorted = tys;
+    a.n = bl.n;
+    a.mode = mode;
+    a.forces_out = forces;
+    a.status = status;
+    auto eval_forces = [&]() -> cudaError_t {
+        cudaError_t r = launch_build_cells_batched(pq, type, b, cs, pm, pqs, tys, ws, run, status, s);
+        if (r != cudaSuccess) return r;
+        return launch_forces_batched(a, b, pair_count, ws, run, s);
+    };
+    if (!forces_valid) {
+        if (launch_drift_wrap_batched(pos, vel, q, b, 0.0, pq, status, s) != cudaSuccess) return MD_ERR_CUDA;
+        if (eval_forces() != cudaSuccess) return MD_ERR_CUDA;
+    }
+    const double half_dt = 0.5 * dt_fs;
+    for (int st = 0; st < n_steps; ++st) {
+        if (launch_kick(vel, forces, mode, inv_mass, bl.n, half_dt, s) != cudaSuccess) return MD_ERR_CUDA;
+        if (launch_drift_wrap_batched(pos, vel, q, b, dt_fs, pq, status, s) != cudaSuccess) return MD_ERR_CUDA;
+        if (eval_forces() != cudaSuccess) return MD_ERR_CUDA;
+        if (launch_kick(vel, forces, mode, inv_mass, bl.n, half_dt, s) != cudaSuccess) return MD_ERR_CUDA;
     }
     return MD_OK;
 }

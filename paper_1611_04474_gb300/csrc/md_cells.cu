@@ -39,26 +39,33 @@ __device__ __forceinline__ int cell_of(const float4 &p, const BoxF &box, uint32_
 
 // Per-block histogram in shared memory (grids with up to kSmemCells cells), then one
 // global add per touched cell; larger grids count with warp-aggregated global atomics.
-template <bool SMEM>
+// Batched: every atom's box comes from its system and cells are numbered globally.
+template <bool SMEM, bool BATCHED>
 __global__ void __launch_bounds__(kIndexThreads)
-k_cell_index(const float4 *__restrict__ pos_q, int n, BoxF box, int *__restrict__ cell_id,
-             int *__restrict__ cell_cnt, uint32_t *status)
+k_cell_index(const float4 *__restrict__ pos_q, int n, BoxF box, BatchArgs b,
+             int *__restrict__ cell_id, int *__restrict__ cell_cnt, uint32_t *status)
 {
     extern __shared__ int s_hist[];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int ncell = BATCHED ? b.ncell : box.ncell;
     if (SMEM) {
-        for (int t = threadIdx.x; t < box.ncell; t += blockDim.x) s_hist[t] = 0;
+        for (int t = threadIdx.x; t < ncell; t += blockDim.x) s_hist[t] = 0;
         __syncthreads();
     }
     int c = -1;
     if (i < n) {
-        c = cell_of(pos_q[i], box, status);
+        if (BATCHED) {
+            const SysDesc &d = b.sys[b.atom_sys[i]];
+            c = d.cell_offset + cell_of(pos_q[i], d.box, status);
+        } else {
+            c = cell_of(pos_q[i], box, status);
+        }
         cell_id[i] = c;
     }
     if (SMEM) {
         if (c >= 0) atomicAdd(&s_hist[c], 1);
         __syncthreads();
-        for (int t = threadIdx.x; t < box.ncell; t += blockDim.x)
+        for (int t = threadIdx.x; t < ncell; t += blockDim.x)
             if (s_hist[t]) atomicAdd(&cell_cnt[t], s_hist[t]);
     } else {
         const unsigned act = __ballot_sync(0xffffffffu, c >= 0);
@@ -138,14 +145,16 @@ __device__ __forceinline__ void place(int e, int slot, const float4 *__restrict_
     type_sorted[slot] = type[e];
 }
 
+template <bool BATCHED>
 __global__ void __launch_bounds__(kSortThreads)
 k_cell_sort(const int *__restrict__ cell_start, const int *__restrict__ perm_tmp,
-            const float4 *__restrict__ pos_q, const int32_t *__restrict__ type, BoxF box,
-            int32_t *__restrict__ perm, float4 *__restrict__ pos_q_sorted,
+            const float4 *__restrict__ pos_q, const int32_t *__restrict__ type, BoxF box_in,
+            BatchArgs b, int32_t *__restrict__ perm, float4 *__restrict__ pos_q_sorted,
             int32_t *__restrict__ type_sorted)
 {
     __shared__ int chunk[kSortChunk];
     const int c = blockIdx.x;
+    const BoxF &box = BATCHED ? b.sys[b.cell_sys[c]].box : box_in;
     const int s0 = cell_start[c];
     const int m = cell_start[c + 1] - s0;
     if (m == 0) return;
@@ -187,19 +196,49 @@ cudaError_t launch_build_cells(const float4 *pos_q, const int32_t *type, int n, 
     int *perm_tmp = reinterpret_cast<int *>(wsp + ws.perm_tmp);
     cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)box.ncell, stream);
     if (e != cudaSuccess) return e;
+    BatchArgs nob = {};
     if (n > 0) {
         int g = (n + kIndexThreads - 1) / kIndexThreads;
         if (box.ncell <= kSmemCells)
-            k_cell_index<true><<<g, kIndexThreads, sizeof(int) * box.ncell, stream>>>(pos_q, n, box, cell_id, cnt, status);
+            k_cell_index<true, false><<<g, kIndexThreads, sizeof(int) * box.ncell, stream>>>(pos_q, n, box, nob, cell_id, cnt, status);
         else
-            k_cell_index<false><<<g, kIndexThreads, 0, stream>>>(pos_q, n, box, cell_id, cnt, status);
+            k_cell_index<false, false><<<g, kIndexThreads, 0, stream>>>(pos_q, n, box, nob, cell_id, cnt, status);
     }
     k_scan_cells<<<1, kScanThreads, 0, stream>>>(cnt, box.ncell, cell_start);
     if (n > 0) {
         int g = (n + kIndexThreads - 1) / kIndexThreads;
         k_scatter<<<g, kIndexThreads, 0, stream>>>(cell_id, n, cnt, perm_tmp);
-        k_cell_sort<<<box.ncell, kSortThreads, 0, stream>>>(cell_start, perm_tmp, pos_q, type, box,
-                                                             perm, pos_q_sorted, type_sorted);
+        k_cell_sort<false><<<box.ncell, kSortThreads, 0, stream>>>(cell_start, perm_tmp, pos_q, type, box,
+                                                                    nob, perm, pos_q_sorted, type_sorted);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_cells_batched(const float4 *pos_q, const int32_t *type, const BatchArgs &b,
+                                       int32_t *cell_start, int32_t *perm, float4 *pos_q_sorted,
+                                       int32_t *type_sorted, const WsLayout &ws, char *wsp,
+                                       uint32_t *status, cudaStream_t stream)
+{
+    int *cell_id = reinterpret_cast<int *>(wsp + ws.cell_id);
+    int *cnt = reinterpret_cast<int *>(wsp + ws.cell_cnt);
+    int *perm_tmp = reinterpret_cast<int *>(wsp + ws.perm_tmp);
+    cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)b.ncell, stream);
+    if (e != cudaSuccess) return e;
+    BoxF nobox = {};
+    const int n = b.n;
+    if (n > 0) {
+        int g = (n + kIndexThreads - 1) / kIndexThreads;
+        if (b.ncell <= kSmemCells)
+            k_cell_index<true, true><<<g, kIndexThreads, sizeof(int) * b.ncell, stream>>>(pos_q, n, nobox, b, cell_id, cnt, status);
+        else
+            k_cell_index<false, true><<<g, kIndexThreads, 0, stream>>>(pos_q, n, nobox, b, cell_id, cnt, status);
+    }
+    k_scan_cells<<<1, kScanThreads, 0, stream>>>(cnt, b.ncell, cell_start);
+    if (n > 0) {
+        int g = (n + kIndexThreads - 1) / kIndexThreads;
+        k_scatter<<<g, kIndexThreads, 0, stream>>>(cell_id, n, cnt, perm_tmp);
+        k_cell_sort<true><<<b.ncell, kSortThreads, 0, stream>>>(cell_start, perm_tmp, pos_q, type, nobox,
+                                                                 b, perm, pos_q_sorted, type_sorted);
     }
     return cudaGetLastError();
 }

@@ -107,9 +107,14 @@ __device__ bool cell_pair(const BoxF &box, int c, int k, PairGeom &g)
     return true;
 }
 
+// Box constants the per-pair minimum image needs.
+struct MiBox {
+    float Lhi[3], Llo[3], invL[3];
+};
+
 template <bool MI>
 __device__ __forceinline__ void displacement(const float4 &pi, const float4 &pj, const PairGeom &g,
-                                             const BoxF &box, float &dx, float &dy, float &dz)
+                                             const MiBox &box, float &dx, float &dy, float &dz)
 {
     if (MI) {
         dx = min_image_f32(pi.x, pj.x, box.Lhi[0], box.Llo[0], box.invL[0]);
@@ -231,8 +236,9 @@ __device__ __forceinline__ void smem_add(typename AccT<MODE>::T *p, typename Acc
         atomicAdd(reinterpret_cast<float *>(p), (float)v);
 }
 
-template <int MODE, bool ENERGY, bool MI>
-__global__ void __launch_bounds__(kHT, 8) k_half_shell(HalfArgs a)
+template <int MODE, bool ENERGY, bool MI, bool BATCHED>
+__global__ void __launch_bounds__(kHT, 8)
+k_half_shell(HalfArgs a, BatchArgs b, unsigned long long *sys_pair_count)
 {
     using Acc = typename AccT<MODE>::T;
     constexpr int CAP = KCap<MODE>::value;
@@ -255,12 +261,40 @@ __global__ void __launch_bounds__(kHT, 8) k_half_shell(HalfArgs a)
     float2 *s_ab = reinterpret_cast<float2 *>(s_dyn + sizeof(Acc) * kHW * 3 * CAP);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int T = a.ntypes;
     float e_lj = 0.f, e_c = 0.f, vir = 0.f;
     unsigned long long cnt = 0;
 
+    // the system this CTA works on: the only one, or the one its cell belongs to
     PairGeom g;
-    const bool valid = cell_pair(a.box, blockIdx.x, blockIdx.y, g);
+    bool valid;
+    int T, sid = 0;
+    const float2 *AB;
+    float kc, rc2, rc2m;
+    MiBox mb;
+    if (BATCHED) {
+        const int cell = b.cell_list[(MI ? b.ncell_reg : 0) + blockIdx.x];
+        sid = b.cell_sys[cell];
+        const SysDesc &d = b.sys[sid];
+        valid = cell_pair(d.box, cell - d.cell_offset, blockIdx.y, g);
+        g.home += d.cell_offset;
+        g.nbr += d.cell_offset;
+        T = d.ntypes;
+        AB = d.AB;
+        kc = d.kc;
+        rc2 = d.rc2;
+        rc2m = d.rc2m;
+        if (MI)
+            for (int k = 0; k < 3; ++k) { mb.Lhi[k] = d.box.Lhi[k]; mb.Llo[k] = d.box.Llo[k]; mb.invL[k] = d.box.invL[k]; }
+    } else {
+        valid = cell_pair(a.box, blockIdx.x, blockIdx.y, g);
+        T = a.ntypes;
+        AB = a.AB;
+        kc = a.kc;
+        rc2 = a.rc2;
+        rc2m = a.rc2m;
+        if (MI)
+            for (int k = 0; k < 3; ++k) { mb.Lhi[k] = a.box.Lhi[k]; mb.Llo[k] = a.box.Llo[k]; mb.invL[k] = a.box.invL[k]; }
+    }
     if (!valid) {
         block_partial<kHT>(0.0, 0.0, 0.0, 0ull, a.partials + (size_t)blockIdx.y * gridDim.x);
         return;
@@ -271,7 +305,7 @@ __global__ void __launch_bounds__(kHT, 8) k_half_shell(HalfArgs a)
         block_partial<kHT>(0.0, 0.0, 0.0, 0ull, a.partials + (size_t)blockIdx.y * gridDim.x);
         return;
     }
-    for (int t = threadIdx.x; t < T * T; t += kHT) s_ab[t] = a.AB[t];
+    for (int t = threadIdx.x; t < T * T; t += kHT) s_ab[t] = AB[t];
     uint16_t *q = s_q[warp];
     Acc(*fb)[CAP] = s_fb[warp];
 
@@ -348,7 +382,7 @@ __global__ void __launch_bounds__(kHT, 8) k_half_shell(HalfArgs a)
             Acc ax = Acc(0), ay = Acc(0), az = Acc(0);  // i-side sums while the row block stays
             float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
             unsigned long long xi2 = 0ull, yi2 = 0ull, zi2 = 0ull;
-            const unsigned long long nrc2 = f2_dup(-a.rc2m);
+            const unsigned long long nrc2 = f2_dup(-rc2m);
             for (int it = warp; it < nitems; it += kHW) {
                 int ib, jb;
                 if (diag) {
@@ -382,7 +416,7 @@ __global__ void __launch_bounds__(kHT, 8) k_half_shell(HalfArgs a)
                     const float gx = fmaxf(0.f, fmaxf(hb[0] - nb[3], nb[0] - hb[3]));
                     const float gy = fmaxf(0.f, fmaxf(hb[1] - nb[4], nb[1] - hb[4]));
                     const float gz = fmaxf(0.f, fmaxf(hb[2] - nb[5], nb[2] - hb[5]));
-                    if (gx * gx + gy * gy + gz * gz >= a.rc2m) continue;
+                    if (gx * gx + gy * gy + gz * gz >= rc2m) continue;
                 }
                 // ---- filter: bit jj of keep <-> neighbour slot jb*32 + jj
                 unsigned keep;
@@ -393,8 +427,8 @@ __global__ void __launch_bounds__(kHT, 8) k_half_shell(HalfArgs a)
                         const int jt = jb * 32 + jj;
                         const float4 pj = make_float4(s_nxyz[0][jt], s_nxyz[1][jt], s_nxyz[2][jt], 0.f);
                         float dx, dy, dz;
-                        displacement<true>(pi, pj, g, a.box, dx, dy, dz);
-                        const float s = fmaf(-dz, dz, fmaf(-dy, dy, fmaf(-dx, dx, a.rc2m)));
+                        displacement<true>(pi, pj, g, mb, dx, dy, dz);
+                        const float s = fmaf(-dz, dz, fmaf(-dy, dy, fmaf(-dx, dx, rc2m)));
                         // (fail << 1) | sign(s): a negative s rejects the candidate
                         fail = __funnelshift_l(__float_as_uint(s), fail, 1);
                     }
@@ -474,11 +508,11 @@ __global__ void __launch_bounds__(kHT, 8) k_half_shell(HalfArgs a)
                         const float4 pa = make_float4(s_hxyz[0][il], s_hxyz[1][il], s_hxyz[2][il], s_hq[il]);
                         const float4 pb = make_float4(s_nxyz[0][jl], s_nxyz[1][jl], s_nxyz[2][jl], s_nq[jl]);
                         float dx, dy, dz;
-                        displacement<MI>(pa, pb, g, a.box, dx, dy, dz);
+                        displacement<MI>(pa, pb, g, mb, dx, dy, dz);
                         const float r2 = pair_r2(dx, dy, dz);
-                        const bool ok = act && (r2 < a.rc2);
+                        const bool ok = act && (r2 < rc2);
                         const float2 ab = s_ab[s_ht[il] * T + s_nt[jl]];
-                        const float kqq = __fmul_rn(a.kc, __fmul_rn(pa.w, pb.w));
+                        const float kqq = __fmul_rn(kc, __fmul_rn(pa.w, pb.w));
                         float ir, ir2, ir6;
                         float f = pair_f(r2, ab.x, ab.y, kqq, ir, ir2, ir6);
                         f = ok ? f : 0.0f;
@@ -577,8 +611,10 @@ __global__ void __launch_bounds__(kHT, 8) k_half_shell(HalfArgs a)
             }
         }
     }
-    block_partial<kHT>((double)e_lj, (double)e_c, (double)vir, cnt,
-                       a.partials + (size_t)blockIdx.y * gridDim.x);
+    Partial *mine = a.partials + (size_t)blockIdx.y * gridDim.x;
+    block_partial<kHT>((double)e_lj, (double)e_c, (double)vir, cnt, mine);
+    if (BATCHED && sys_pair_count && threadIdx.x == 0 && mine[blockIdx.x].count)
+        atomicAdd(&sys_pair_count[sid], mine[blockIdx.x].count);
 }
 
 // Sorted-order accumulators -> forces_out in input order.
@@ -606,8 +642,9 @@ k_finalize(const void *__restrict__ accum, const int32_t *__restrict__ perm, int
     }
 }
 
-template <int MODE, bool ENERGY, bool MI>
-void launch_half_t(const HalfArgs &h, dim3 grid, cudaStream_t stream)
+template <int MODE, bool ENERGY, bool MI, bool BATCHED = false>
+void launch_half_t(const HalfArgs &h, dim3 grid, cudaStream_t stream, const BatchArgs &b = BatchArgs{},
+                   unsigned long long *sys_pair_count = nullptr)
 {
     using Acc = typename AccT<MODE>::T;
     const size_t dyn = sizeof(Acc) * kHW * 3 * KCap<MODE>::value +
@@ -615,9 +652,9 @@ void launch_half_t(const HalfArgs &h, dim3 grid, cudaStream_t stream)
     static const size_t dyn_max = sizeof(Acc) * kHW * 3 * KCap<MODE>::value +
                                   sizeof(float2) * kMaxTypes * kMaxTypes;
     static const cudaError_t attr = cudaFuncSetAttribute(
-        k_half_shell<MODE, ENERGY, MI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);
+        k_half_shell<MODE, ENERGY, MI, BATCHED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);
     (void)attr;
-    k_half_shell<MODE, ENERGY, MI><<<grid, kHT, dyn, stream>>>(h);
+    k_half_shell<MODE, ENERGY, MI, BATCHED><<<grid, kHT, dyn, stream>>>(h, b, sys_pair_count);
 }
 
 }  // namespace
@@ -626,6 +663,58 @@ void launch_half_t(const HalfArgs &h, dim3 grid, cudaStream_t stream)
 int half_shell_pairs_per_cell(const BoxF &box)
 {
     return (box.dims[0] < 3 || box.dims[1] < 3 || box.dims[2] < 3) ? 27 : 14;
+}
+
+// rc^2 of the exact test and the filter threshold rc'^2: the filter may see a
+// difference short by |Llo| per wrapped axis and rounds differently from the exact
+// test, so it is widened by that much and a few ulps.
+void cutoff_thresholds(const BoxF &box, double rc, bool mi, float *rc2, float *rc2m)
+{
+    *rc2 = (float)(rc * rc);
+    const double llo = fabs((double)box.Llo[0]) + fabs((double)box.Llo[1]) + fabs((double)box.Llo[2]);
+    const double margin = mi ? 0.0 : 2.0 * rc * llo * 1.01 + 3.0 * llo * llo;
+    *rc2m = (float)((double)*rc2 + margin + 8.0 * (double)*rc2 * 1.1920929e-7);
+}
+
+cudaError_t launch_forces_batched(const ForceArgs &a, const BatchArgs &b,
+                                  unsigned long long *sys_pair_count, const WsLayout &ws,
+                                  char *wsp, cudaStream_t stream)
+{
+    Partial *partials = reinterpret_cast<Partial *>(wsp + ws.partials);
+    const size_t acc_bytes = (size_t)b.n * (a.mode == MD_ACCUM_FIXED64 ? 24 : 16);
+    void *accum = wsp + ws.accum;
+    cudaError_t e = cudaMemsetAsync(accum, 0, acc_bytes, stream);
+    if (e != cudaSuccess) return e;
+    HalfArgs h = {};
+    h.cell_start = a.cell_start;
+    h.pq = a.pos_q_sorted;
+    h.ty = a.type_sorted;
+    h.accum = accum;
+    h.n = b.n;
+    h.status = a.status;
+    // the shared LJ table must hold the largest table of the batch
+    h.ntypes = b.max_ntypes;
+    if (h.ntypes < 1 || h.ntypes > kMaxTypes) return cudaErrorInvalidValue;
+    if (b.ncell_reg > 0) {
+        h.partials = partials;
+        dim3 grid(b.ncell_reg, 14);
+        if (a.mode == MD_ACCUM_FIXED64) launch_half_t<MD_ACCUM_FIXED64, false, false, true>(h, grid, stream, b, sys_pair_count);
+        else launch_half_t<MD_ACCUM_F32, false, false, true>(h, grid, stream, b, sys_pair_count);
+    }
+    if (b.ncell_mi > 0) {
+        h.partials = partials + (size_t)14 * b.ncell_reg;
+        dim3 grid(b.ncell_mi, 27);
+        if (a.mode == MD_ACCUM_FIXED64) launch_half_t<MD_ACCUM_FIXED64, false, true, true>(h, grid, stream, b, sys_pair_count);
+        else launch_half_t<MD_ACCUM_F32, false, true, true>(h, grid, stream, b, sys_pair_count);
+    }
+    const int g = (b.n + 255) / 256;
+    if (g > 0) {
+        if (a.mode == MD_ACCUM_FIXED64)
+            k_finalize<MD_ACCUM_FIXED64><<<g, 256, 0, stream>>>(accum, a.perm, b.n, a.forces_out, a.status);
+        else
+            k_finalize<MD_ACCUM_F32><<<g, 256, 0, stream>>>(accum, a.perm, b.n, a.forces_out, a.status);
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_half_shell(const ForceArgs &a, const WsLayout &ws, char *wsp, Partial *partials,
@@ -645,13 +734,7 @@ cudaError_t launch_half_shell(const ForceArgs &a, const WsLayout &ws, char *wsp,
     h.AB = a.AB;
     h.ntypes = a.ntypes;
     h.kc = a.k_coulomb;
-    const float rc2 = (float)(a.rc64 * a.rc64);
-    // the filter may see a difference short by |Llo| per wrapped axis and rounds
-    // differently from the exact test: widen it by that much and a few ulps
-    const double llo = fabs((double)a.box.Llo[0]) + fabs((double)a.box.Llo[1]) + fabs((double)a.box.Llo[2]);
-    const double margin = mi ? 0.0 : 2.0 * a.rc64 * llo * 1.01 + 3.0 * llo * llo;
-    h.rc2 = rc2;
-    h.rc2m = (float)((double)rc2 + margin + 8.0 * (double)rc2 * 1.1920929e-7);
+    cutoff_thresholds(a.box, a.rc64, mi, &h.rc2, &h.rc2m);
     h.accum = accum;
     h.n = a.n;
     h.partials = partials;

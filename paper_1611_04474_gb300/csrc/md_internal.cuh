@@ -37,6 +37,21 @@ struct BoxF {
 
 BoxF make_box(const double *L, const int32_t *dims);
 
+// One system of a batch as the kernels see it (device array in the batch workspace).
+struct SysDesc {
+    BoxF box;
+    const float2 *AB;
+    int ntypes;
+    float kc;
+    double kc64;
+    float rc2, rc2m;   // exact cutoff test, conservative filter threshold
+    int atom_offset;   // first atom (input order and sorted order alike)
+    int natoms;
+    int cell_offset;   // first global cell
+    int mi;            // some axis has two cells: per-pair minimum image
+};
+
+
 struct WsLayout {
     size_t cell_id;     // int32 [n]          cell of each input atom
     size_t cell_cnt;    // int32 [ncell]      per-cell counts, then scatter cursors
@@ -50,6 +65,18 @@ struct WsLayout {
 };
 
 WsLayout ws_layout(int n, int ncell);
+
+// Layout of the batch workspace (byte offsets), derived on the host from the systems.
+struct BatchLayout {
+    int nsys, n, ncell, ncell_mi, ncell_reg;
+    size_t sys;         // SysDesc [nsys]
+    size_t cell_sys;    // int [ncell]: system of each global cell
+    size_t cell_list;   // int [ncell]: regular systems' cells, then minimum-image ones
+    size_t atom_sys;    // int [n]: system of each atom
+    WsLayout run;       // the per-run scratch of the single-system path, sized for n, ncell
+    size_t run_base;    // where that scratch starts
+    size_t total;
+};
 
 // ----------------------------------------------------------------- device helpers
 
@@ -225,8 +252,29 @@ struct ForceArgs {
 
 cudaError_t launch_forces(const ForceArgs &a, const WsLayout &ws, char *wsp, cudaStream_t stream);
 int half_shell_pairs_per_cell(const BoxF &box);
+void cutoff_thresholds(const BoxF &box, double rc, bool mi, float *rc2, float *rc2m);
 cudaError_t launch_half_shell(const ForceArgs &a, const WsLayout &ws, char *wsp, Partial *partials,
                               int *nblocks_out, cudaStream_t stream);
+
+// Batched forms: every system of the batch in one launch per kernel.
+struct BatchArgs {
+    const SysDesc *sys;
+    const int *cell_sys;
+    const int *cell_list;
+    const int *atom_sys;
+    int nsys, n, ncell, ncell_mi, ncell_reg;
+    int max_ntypes;  // largest LJ table of the batch: sizes the kernels' shared copy
+};
+cudaError_t launch_build_cells_batched(const float4 *pos_q, const int32_t *type, const BatchArgs &b,
+                                       int32_t *cell_start, int32_t *perm, float4 *pos_q_sorted,
+                                       int32_t *type_sorted, const WsLayout &ws, char *wsp,
+                                       uint32_t *status, cudaStream_t stream);
+cudaError_t launch_forces_batched(const ForceArgs &a, const BatchArgs &b,
+                                  unsigned long long *sys_pair_count, const WsLayout &ws,
+                                  char *wsp, cudaStream_t stream);
+cudaError_t launch_drift_wrap_batched(double *pos, const double *vel, const float *q, const BatchArgs &b,
+                                      double dt, float4 *pos_q_out, uint32_t *status,
+                                      cudaStream_t stream);
 
 cudaError_t launch_kick(double *vel, const void *forces, int mode, const float *inv_mass, int n,
                         double half_dt, cudaStream_t stream);

@@ -68,6 +68,32 @@ k_drift_wrap(double *__restrict__ pos, const double *__restrict__ vel, const flo
     pos_q_out[i] = make_float4((float)x[0], (float)x[1], (float)x[2], q[i]);
 }
 
+// The same for a batch: each atom wraps into its own system's box.
+__global__ void __launch_bounds__(kThreads)
+k_drift_wrap_batched(double *__restrict__ pos, const double *__restrict__ vel,
+                     const float *__restrict__ q, BatchArgs b, double dt,
+                     float4 *__restrict__ pos_q_out, uint32_t *status)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= b.n) return;
+    const BoxF &box = b.sys[b.atom_sys[i]].box;
+    double x[3];
+    bool ok = true;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        double v = pos[3 * i + c] + dt * vel[3 * i + c];
+        if (isfinite(v)) {
+            v = wrap_coord(v, box.L[c]);
+        } else {
+            ok = false;
+        }
+        x[c] = v;
+        pos[3 * i + c] = v;
+    }
+    if (!ok) set_status(status, MD_STATUS_NONFINITE);
+    pos_q_out[i] = make_float4((float)x[0], (float)x[1], (float)x[2], q[i]);
+}
+
 // Per-block kinetic energy 1/2 m v^2 (kcal/mol) into partials[blockIdx.x].e_lj.
 __global__ void __launch_bounds__(kThreads)
 k_kinetic(const double *__restrict__ vel, const float *__restrict__ inv_mass, int n,
@@ -132,6 +158,16 @@ cudaError_t launch_drift_wrap(double *pos, const double *vel, const float *q, in
     if (n <= 0) return cudaSuccess;
     k_drift_wrap<<<(n + kThreads - 1) / kThreads, kThreads, 0, stream>>>(pos, vel, q, n, box, dt,
                                                                          pos_q_out, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_drift_wrap_batched(double *pos, const double *vel, const float *q, const BatchArgs &b,
+                                      double dt, float4 *pos_q_out, uint32_t *status,
+                                      cudaStream_t stream)
+{
+    if (b.n <= 0) return cudaSuccess;
+    k_drift_wrap_batched<<<(b.n + kThreads - 1) / kThreads, kThreads, 0, stream>>>(pos, vel, q, b, dt,
+                                                                                  pos_q_out, status);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,86 @@
+"""Batched many-system throughput: the systems advanced together through md_batch_step
+(optionally replayed from a captured CUDA graph), against advancing each system alone
+with md_step one after the other on the same GPU.
+
+    python -m paper_1611_04474_gb300.run_batch --nsys 256 --steps 50 --mode fixed64
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+import torch
+
+from . import api
+from . import workloads as W
+
+
+def _time(fn, reps=1):
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--nsys", type=int, default=256)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--seed", type=int, default=4)
+    ap.add_argument("--mode", default="fixed64", choices=["f32", "fixed64"])
+    ap.add_argument("--no-alone", action="store_true")
+    args = ap.parse_args(argv)
+    mode = api.ACCUM_F32 if args.mode == "f32" else api.ACCUM_FIXED64
+    systems = W.batch_of_systems(nsys=args.nsys, seed=args.seed)
+    out = {"nsys": args.nsys, "atoms": sum(s.n for s in systems), "steps": args.steps,
+           "mode": args.mode, "rc_clamped": sum(bool(s.meta["rc_clamped"]) for s in systems)}
+
+    b = api.Batch(systems, mode=mode)
+    b.step(1, count_pairs=True)  # forces of the start state + one step, outside timing
+    torch.cuda.synchronize()
+    b.pair_count.zero_()
+    t_loop = _time(lambda: b.step(args.steps, count_pairs=True))
+    pairs = float(b.pair_count.sum().item())
+    out["batch_loop_ms"] = t_loop
+    out["pairs_per_s_batch_loop"] = pairs / (t_loop / 1e3)
+
+    # the same steps captured once in a CUDA graph and replayed
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        b.step(1)  # warm-up on the capture stream
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=s):
+            b.step(args.steps, count_pairs=True)
+    torch.cuda.synchronize()
+    b.pair_count.zero_()
+    t_graph = _time(lambda: g.replay())
+    out["batch_graph_ms"] = t_graph
+    out["pairs_per_s_batch_graph"] = float(b.pair_count.sum().item()) / (t_graph / 1e3)
+    out["md_steps_per_s_per_system_graph"] = args.steps / (t_graph / 1e3)
+    out["status"] = int(b.status.item())
+
+    if not args.no_alone:
+        engines = [api.Engine(sy, mode=mode) for sy in systems]
+        for e in engines:
+            e.step(1)
+        torch.cuda.synchronize()
+
+        def alone():
+            for e in engines:
+                e.step(args.steps)
+
+        t_alone = _time(alone)
+        out["alone_ms"] = t_alone
+        out["pairs_per_s_alone"] = pairs / (t_alone / 1e3)
+        out["speedup_graph_vs_alone"] = t_alone / t_graph
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -237,3 +237,47 @@ def sweep_sizes():
     """Atom counts of the size sweep at ApoA1 density: 92,224 x {1/4, 1, 4, 16}."""
     return [APOA1_N // 4, APOA1_N, APOA1_N * 4, APOA1_N * 16]
 
+
+
+def batch_of_systems(nsys: int = 256, seed: int = 4, n_range=(500, 20000), rho_range=(0.08, 0.11),
+                     type_range=(4, 8), rc_range=(9.0, 12.0), sigma_range=(1.9, 2.3),
+                     eps_range=(0.05, 0.2), mass_range=(12.0, 16.0), charge_sd: float = 0.2,
+                     jitter: float = 0.3):
+    """Independent periodic systems of uneven size for the batched path.
+
+    Atom counts are log-uniform in n_range, densities uniform in rho_range, boxes cubic
+    with L = (N / rho)^(1/3), 4-8 LJ types, cutoffs uniform in rc_range.  A cutoff at or
+    above L/2 (the minimum image would be ambiguous) is lowered to 0.999 L/2; such
+    systems are listed in meta['rc_clamped'].  Atoms sit on a jittered cubic lattice
+    (no overlaps); LJ diameters of 1.9-2.3 A against charges ~N(0, 0.2) e keep opposite
+    charges from collapsing through each other during the run, so the int64 fixed-point
+    pair terms stay in range."""
+    rng = np.random.default_rng(seed)
+    systems = []
+    lo, hi = np.log(n_range[0]), np.log(n_range[1])
+    for k in range(nsys):
+        n = int(round(np.exp(rng.uniform(lo, hi))))
+        rho = rng.uniform(*rho_range)
+        L = (n / rho) ** (1.0 / 3.0)
+        box = np.array([L, L, L])
+        m = int(np.ceil(n ** (1.0 / 3.0)))
+        g = np.stack(np.meshgrid(np.arange(m), np.arange(m), np.arange(m), indexing="ij"), -1)
+        g = g.reshape(-1, 3).astype(np.float64)
+        keep = np.sort(rng.permutation(g.shape[0])[:n])
+        spacing = L / m
+        pos = (g[keep] + 0.5) * spacing + rng.uniform(-jitter, jitter, size=(n, 3))
+        ntypes = int(rng.integers(type_range[0], type_range[1] + 1))
+        rc_drawn = rng.uniform(*rc_range)
+        rc = float(np.float32(min(rc_drawn, 0.999 * L / 2)))
+        sigma = rng.uniform(*sigma_range, size=ntypes)
+        eps = rng.uniform(*eps_range, size=ntypes)
+        types = rng.integers(0, ntypes, size=n).astype(np.int32)
+        q = rng.normal(0.0, charge_sd, size=n)
+        q -= q.mean()
+        mass = rng.uniform(*mass_range, size=n).astype(np.float32)
+        vel = maxwell_velocities(rng, mass, 300.0)
+        systems.append(System(f"batch_{k}", to_f32_in_box(pos, box), q.astype(np.float32), types,
+                              box, rc, sigma, eps, lj_table(sigma, eps), mass, vel,
+                              meta=dict(seed=seed, index=k, rho=rho, rc_drawn=rc_drawn,
+                                        rc_clamped=rc < rc_drawn - 1e-6)))
+    return systems

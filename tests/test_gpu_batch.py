@@ -1,0 +1,72 @@
+"""Batched systems (md_batch_*): every system's result in the batch equals running it
+alone, bit for bit in FIXED64, and matches the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1611_04474_gb300 import workloads as W
+from tests.parity import boundary_alternatives, force_errors
+
+pytestmark = pytest.mark.gpu
+
+
+def _systems():
+    # small boxes (an axis of two cells: per-pair minimum image) and larger ones together
+    return W.batch_of_systems(nsys=10, seed=7, n_range=(400, 6000))
+
+
+def _alone(api, s, mode, n_steps):
+    eng = api.Engine(s, mode=mode)
+    eng.step(n_steps, dt_fs=1.0) if n_steps else eng.step(0, dt_fs=1.0)
+    torch.cuda.synchronize()
+    return eng
+
+
+def test_batch_mixes_both_cell_regimes():
+    from paper_1611_04474_gb300 import api  # noqa: F401 (import only)
+
+    dims = [np.floor(s.box / s.rc) for s in _systems()]
+    assert any(d.min() < 3 for d in dims) and any(d.min() >= 3 for d in dims)
+
+
+@pytest.mark.parametrize("n_steps", [0, 4])
+def test_fixed64_batch_is_bitwise_the_single_system_path(cuda_lib, n_steps):
+    api = cuda_lib
+    systems = _systems()
+    b = api.Batch(systems, mode=api.ACCUM_FIXED64)
+    b.step(n_steps, dt_fs=1.0, count_pairs=True)
+    torch.cuda.synchronize()
+    assert int(b.status.item()) == 0
+    Fb = b.forces.cpu().numpy()
+    Xb = b.pos.cpu().numpy()
+    Vb = b.vel.cpu().numpy()
+    counts = b.pair_count.cpu().numpy()
+    for k, s in enumerate(systems):
+        eng = _alone(api, s, api.ACCUM_FIXED64, n_steps)
+        sl = b.system_slice(k)
+        assert np.array_equal(Fb[sl], eng.forces.cpu().numpy()), k
+        assert np.array_equal(Xb[sl], eng.pos.cpu().numpy()), k
+        assert np.array_equal(Vb[sl], eng.vel.cpu().numpy()), k
+        eng.build_cells()
+        eng.compute_forces(count=True)
+        torch.cuda.synchronize()
+        if n_steps == 0:
+            assert counts[k] == int(eng.pair_count.item()), k
+
+
+def test_f32_batch_matches_oracle(cuda_lib):
+    api = cuda_lib
+    systems = _systems()
+    b = api.Batch(systems, mode=api.ACCUM_F32)
+    b.step(0)
+    torch.cuda.synchronize()
+    F = b.forces.cpu().numpy().astype(np.float64)
+    for k in (0, 3, 9):
+        s = systems[k]
+        ff = oracle.ForceField.from_system(s)
+        p = s.pos.astype(np.float64)
+        ref = oracle.forces_cells(p, s.q, s.type, s.box, ff)
+        alts, nb = boundary_alternatives(p, s, ff, ref.F)
+        err = force_errors(F[b.system_slice(k)], ref.F, ref.cond, alts)
+        assert err["max_norm"] <= 1e-5, (k, err)
