@@ -299,15 +299,20 @@ class Engine:
 
 class Batch:
     """Independent systems advanced together (md_batch_*): the systems' arrays are
-    concatenated on the device once; every step is one set of launches for all of them."""
+    concatenated on the device; every step is one set of launches for all of them.
 
-    def __init__(self, systems, mode=ACCUM_FIXED64, device="cuda"):
+    ``state`` (optional) gives the concatenated device arrays directly (keys pos, vel,
+    forces, q, types, inv_mass) so that a caller keeping systems on the device builds a
+    batch without a host round trip; ``ffs`` likewise reuses device force fields."""
+
+    def __init__(self, systems, mode=ACCUM_FIXED64, device="cuda", state=None, ffs=None):
         if mode not in (ACCUM_F32, ACCUM_FIXED64):
             raise ValueError("batched mode must be ACCUM_F32 or ACCUM_FIXED64")
         self.systems = list(systems)
         self.mode = mode
         self.nsys = len(self.systems)
-        self.ffs = [ForceField.from_system(s, device) for s in self.systems]
+        self.ffs = list(ffs) if ffs is not None else [ForceField.from_system(s, device)
+                                                      for s in self.systems]
         self.desc = (md_system_desc * self.nsys)()
         for k, (s, ff) in enumerate(zip(self.systems, self.ffs)):
             self.desc[k].n = s.n
@@ -317,13 +322,24 @@ class Batch:
             self.desc[k].ff = ff._c
         self.offsets = np.concatenate([[0], np.cumsum([s.n for s in self.systems])]).astype(np.int64)
         self.n = int(self.offsets[-1])
-        cat = lambda f, dt: torch.as_tensor(np.concatenate([f(s) for s in self.systems]).astype(dt)).to(device)
-        self.pos = cat(lambda s: s.pos.astype(np.float64), np.float64).contiguous()
-        self.vel = cat(lambda s: s.vel, np.float64).contiguous()
-        self.q = cat(lambda s: s.q, np.float32)
-        self.types = cat(lambda s: s.type, np.int32)
-        self.inv_mass = cat(lambda s: s.inv_mass, np.float32)
-        self.forces = torch.zeros((self.n, 3), dtype=FORCE_DTYPE[mode], device=device)
+        if state is not None:
+            self.pos, self.vel, self.forces = state["pos"], state["vel"], state["forces"]
+            self.q, self.types, self.inv_mass = state["q"], state["types"], state["inv_mass"]
+            for name, t, dt, shape in (("pos", self.pos, torch.float64, (self.n, 3)),
+                                       ("vel", self.vel, torch.float64, (self.n, 3)),
+                                       ("forces", self.forces, FORCE_DTYPE[mode], (self.n, 3)),
+                                       ("q", self.q, torch.float32, (self.n,)),
+                                       ("types", self.types, torch.int32, (self.n,)),
+                                       ("inv_mass", self.inv_mass, torch.float32, (self.n,))):
+                _need(t, dt, shape, name)
+        else:
+            cat = lambda f, dt: torch.as_tensor(np.concatenate([f(s) for s in self.systems]).astype(dt)).to(device)
+            self.pos = cat(lambda s: s.pos.astype(np.float64), np.float64).contiguous()
+            self.vel = cat(lambda s: s.vel, np.float64).contiguous()
+            self.q = cat(lambda s: s.q, np.float32)
+            self.types = cat(lambda s: s.type, np.int32)
+            self.inv_mass = cat(lambda s: s.inv_mass, np.float32)
+            self.forces = torch.zeros((self.n, 3), dtype=FORCE_DTYPE[mode], device=device)
         self.pair_count = torch.zeros(self.nsys, dtype=torch.int64, device=device)
         self.status = torch.zeros(1, dtype=torch.int32, device=device)
         nbytes = int(load().md_batch_workspace_bytes(self.nsys, ctypes.byref(self.desc)))

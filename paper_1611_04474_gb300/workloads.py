@@ -281,3 +281,31 @@ def batch_of_systems(nsys: int = 256, seed: int = 4, n_range=(500, 20000), rho_r
                               meta=dict(seed=seed, index=k, rho=rho, rc_drawn=rc_drawn,
                                         rc_clamped=rc < rc_drawn - 1e-6)))
     return systems
+
+
+def serving_jobs(n_jobs: int = 2000, rate_per_s: float = 200.0, seed: int = 5,
+                 n_range=(1000, 150000), steps_range=(10, 500), rho: float = 0.1,
+                 rc: float = 12.0):
+    """MD jobs arriving as a Poisson stream: (system, n_steps, arrival time in s).
+
+    Atom counts log-uniform in n_range, steps uniform integers in steps_range, density
+    0.1 atoms/A^3 in cubic boxes, cutoff 12 A (lowered to 0.999 L/2 in small boxes),
+    force field as in batch_of_systems.  Systems are drawn lazily (a callable per job),
+    so a long stream does not hold every system in host memory at once."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate_per_s, size=n_jobs))
+    lo, hi = np.log(n_range[0]), np.log(n_range[1])
+    ns = np.round(np.exp(rng.uniform(lo, hi, size=n_jobs))).astype(int)
+    steps = rng.integers(steps_range[0], steps_range[1] + 1, size=n_jobs)
+    seeds = rng.integers(0, 2**31 - 1, size=n_jobs)
+    jobs = []
+    for k in range(n_jobs):
+        n, sd = int(ns[k]), int(seeds[k])
+
+        def make(n=n, sd=sd):
+            s = batch_of_systems(nsys=1, seed=sd, n_range=(n, n), rho_range=(rho, rho),
+                                 rc_range=(rc, rc))[0]
+            s.name = f"job_{sd}"
+            return s
+        jobs.append((make, int(steps[k]), float(t[k]), n))
+    return jobs
