@@ -241,6 +241,33 @@ int md_batch_step(int32_t nsys, const md_system_desc *systems, double *pos, doub
                   unsigned long long *pair_count, void *workspace, size_t ws_bytes,
                   uint32_t *status, void *stream);
 
+/*
+ * Kernel shapes of the batched force launches.  A shape is a performance choice only:
+ * every shape finds the same pairs, and in MD_ACCUM_FIXED64 gives the same bits.
+ *   0  default: 4 warps per block, 256 (F32) or 128 (FIXED64) buffered pairs per warp
+ *   1  2 warps per block, 256 buffered pairs per warp
+ *   2  8 warps per block, 256 buffered pairs per warp
+ *   3  4 warps per block, 128 buffered pairs per warp
+ * The buffer holds the filter's survivors of one 32x32 block of candidate pairs (the
+ * paper's queue between distance and force stages, Section IV); a block that keeps more
+ * is processed in several passes.  More warps per block share the block's staged cells
+ * among more candidate blocks; fewer give more blocks per SM for small cells.
+ */
+#define MD_BATCH_SHAPES 4
+typedef struct md_batch_tuning {
+    int32_t shape_regular; /* launch over the systems with >= 3 cells on every axis */
+    int32_t shape_small;   /* launch over the systems with an axis of 2 cells */
+} md_batch_tuning;
+
+/* md_batch_step with the force launches' shapes chosen by `tuning` (host; NULL = both
+ * 0).  MD_ERR_INVALID_ARG for a shape outside 0 .. MD_BATCH_SHAPES-1. */
+int md_batch_step_tuned(int32_t nsys, const md_system_desc *systems, double *pos, double *vel,
+                        void *forces, int32_t forces_valid, const float *inv_mass,
+                        const float *q, const int32_t *type, int32_t mode, double dt_fs,
+                        int32_t n_steps, unsigned long long *pair_count, void *workspace,
+                        size_t ws_bytes, uint32_t *status, const md_batch_tuning *tuning,
+                        void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,7 +30,8 @@ FIXED_SCALE = 2.0**32
 
 EXPORTS = ("md_strerror", "md_abi_version", "md_cell_dims", "md_workspace_bytes", "md_build_cells",
            "md_build_cells_noalloc", "md_nonbonded_forces", "md_nonbonded_forces_algo", "md_step",
-           "md_batch_workspace_bytes", "md_batch_prepare", "md_batch_step")
+           "md_batch_workspace_bytes", "md_batch_prepare", "md_batch_step", "md_batch_step_tuned")
+BATCH_SHAPES = 4  # MD_BATCH_SHAPES: kernel shapes of the batched force launches
 
 _lib = None
 
@@ -49,6 +50,10 @@ class md_forcefield(ctypes.Structure):
 class md_system_desc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("box_L", ctypes.c_double * 3), ("ff", md_forcefield)]
+
+
+class md_batch_tuning(ctypes.Structure):
+    _fields_ = [("shape_regular", ctypes.c_int32), ("shape_small", ctypes.c_int32)]
 
 
 def load(path: str | None = None):
@@ -85,6 +90,9 @@ def load(path: str | None = None):
     lib.md_batch_prepare.restype = ctypes.c_int
     lib.md_batch_step.argtypes = [i32, P, P, P, P, i32, P, P, P, i32, f64, i32, P, P, sz, P, P]
     lib.md_batch_step.restype = ctypes.c_int
+    lib.md_batch_step_tuned.argtypes = [i32, P, P, P, P, i32, P, P, P, i32, f64, i32, P, P, sz, P,
+                                        P, P]
+    lib.md_batch_step_tuned.restype = ctypes.c_int
     del V
     if path is None:
         _lib = lib
@@ -303,9 +311,13 @@ class Batch:
 
     ``state`` (optional) gives the concatenated device arrays directly (keys pos, vel,
     forces, q, types, inv_mass) so that a caller keeping systems on the device builds a
-    batch without a host round trip; ``ffs`` likewise reuses device force fields."""
+    batch without a host round trip; ``ffs`` likewise reuses device force fields.
+    ``tuning`` = (shape for the systems with >= 3 cells per axis, shape for those with an
+    axis of 2 cells), each in 0 .. BATCH_SHAPES-1 (md_batch_tuning); a performance choice
+    only, see ``autotune``."""
 
-    def __init__(self, systems, mode=ACCUM_FIXED64, device="cuda", state=None, ffs=None):
+    def __init__(self, systems, mode=ACCUM_FIXED64, device="cuda", state=None, ffs=None,
+                 tuning=(0, 0)):
         if mode not in (ACCUM_F32, ACCUM_FIXED64):
             raise ValueError("batched mode must be ACCUM_F32 or ACCUM_FIXED64")
         self.systems = list(systems)
@@ -347,17 +359,19 @@ class Batch:
             raise ValueError("invalid batch (a cutoff at or above L/2, bad n or force field)")
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=device)
         self.forces_valid = False
+        self.tuning = tuple(tuning)
         _check("md_batch_prepare", load().md_batch_prepare(
             self.nsys, ctypes.byref(self.desc), _ptr(self.workspace), nbytes,
             _stream(None)))
 
     def step(self, n_steps=1, dt_fs=1.0, count_pairs=False, stream=None):
-        _check("md_batch_step", load().md_batch_step(
+        t = md_batch_tuning(int(self.tuning[0]), int(self.tuning[1]))
+        _check("md_batch_step_tuned", load().md_batch_step_tuned(
             self.nsys, ctypes.byref(self.desc), _ptr(self.pos), _ptr(self.vel), _ptr(self.forces),
             int(self.forces_valid), _ptr(self.inv_mass), _ptr(self.q), _ptr(self.types),
             int(self.mode), float(dt_fs), int(n_steps),
             _ptr(self.pair_count) if count_pairs else None, _ptr(self.workspace),
-            self.workspace.numel(), _ptr(self.status), _stream(stream)))
+            self.workspace.numel(), _ptr(self.status), ctypes.byref(t), _stream(stream)))
         self.forces_valid = True
 
     def system_slice(self, k):

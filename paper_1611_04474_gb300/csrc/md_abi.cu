@@ -414,6 +414,22 @@ int md_batch_step(int32_t nsys, const md_system_desc *systems, double *pos, doub
                   unsigned long long *pair_count, void *workspace, size_t ws_bytes,
                   uint32_t *status, void *stream)
 {
+    return md_batch_step_tuned(nsys, systems, pos, vel, forces, forces_valid, inv_mass, q, type,
+                               mode, dt_fs, n_steps, pair_count, workspace, ws_bytes, status,
+                               nullptr, stream);
+}
+
+int md_batch_step_tuned(int32_t nsys, const md_system_desc *systems, double *pos, double *vel,
+                        void *forces, int32_t forces_valid, const float *inv_mass,
+                        const float *q, const int32_t *type, int32_t mode, double dt_fs,
+                        int32_t n_steps, unsigned long long *pair_count, void *workspace,
+                        size_t ws_bytes, uint32_t *status, const md_batch_tuning *tuning,
+                        void *stream)
+{
+    const int shape_reg = tuning ? tuning->shape_regular : 0;
+    const int shape_mi = tuning ? tuning->shape_small : 0;
+    if (shape_reg < 0 || shape_reg >= MD_BATCH_SHAPES || shape_mi < 0 || shape_mi >= MD_BATCH_SHAPES)
+        return MD_ERR_INVALID_ARG;
     BatchLayout bl;
     std::vector<int32_t> dims;
     int e = batch_layout(nsys, systems, &bl, &dims);
@@ -459,7 +475,7 @@ int md_batch_step(int32_t nsys, const md_system_desc *systems, double *pos, doub
     auto eval_forces = [&]() -> cudaError_t {
         cudaError_t r = launch_build_cells_batched(pq, type, b, cs, pm, pqs, tys, ws, run, status, s);
         if (r != cudaSuccess) return r;
-        return launch_forces_batched(a, b, pair_count, ws, run, s);
+        return launch_forces_batched(a, b, pair_count, ws, run, s, shape_reg, shape_mi);
     };
     if (!forces_valid) {
         if (launch_drift_wrap_batched(pos, vel, q, b, 0.0, pq, status, s) != cudaSuccess) return MD_ERR_CUDA;

@@ -35,8 +35,7 @@
 namespace mdnb {
 namespace {
 
-constexpr int kHW = 4;               // warps per CTA
-constexpr int kHT = kHW * 32;        // threads per CTA
+constexpr int kHWDefault = 4;        // warps per CTA of the single-system launches
 constexpr int kTile = 256;           // atoms of a cell staged at once (i, j indices fit 8 bits)
 constexpr float kFar = 1.0e18f;      // coordinate of padding slots: fails every filter
 
@@ -197,11 +196,12 @@ __device__ __forceinline__ unsigned transpose32(unsigned x, int lane)
 
 // Bounding box of each 32-atom block of a staged tile (padding slots excluded), one
 // warp per block.  Blocks with no atom get an empty box that is never in range.
+template <int W>
 __device__ __forceinline__ void block_boxes(const float (*xyz)[kTile], int m, int m32,
                                             float (*box)[6])
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int b = warp; b < (m32 >> 5); b += kHW) {
+    for (int b = warp; b < (m32 >> 5); b += W) {
         const int t = b * 32 + lane;
         const bool in = t < m;
 #pragma unroll
@@ -223,7 +223,7 @@ __device__ __forceinline__ void block_boxes(const float (*xyz)[kTile], int m, in
 
 template <int MODE>
 struct KCap {
-    // survivors buffered per pass: one pass holds a typical 32x32 item
+    // survivors buffered per pass (default): one pass holds a typical 32x32 item
     static constexpr int value = MODE == MD_ACCUM_FIXED64 ? 128 : 256;
 };
 
@@ -236,12 +236,15 @@ __device__ __forceinline__ void smem_add(typename AccT<MODE>::T *p, typename Acc
         atomicAdd(reinterpret_cast<float *>(p), (float)v);
 }
 
-template <int MODE, bool ENERGY, bool MI, bool BATCHED>
-__global__ void __launch_bounds__(kHT, 8)
+// W warps per CTA and CAP buffered survivors per warp are the tunable shape; the launch
+// bound keeps 64 registers per thread for every W.
+template <int MODE, bool ENERGY, bool MI, bool BATCHED, int W, int CAP>
+__global__ void __launch_bounds__(W * 32, 32 / W)
 k_half_shell(HalfArgs a, BatchArgs b, unsigned long long *sys_pair_count)
 {
     using Acc = typename AccT<MODE>::T;
-    constexpr int CAP = KCap<MODE>::value;
+    constexpr int kHW = W;
+    constexpr int kHT = W * 32;
     __shared__ __align__(16) float s_hxyz[3][kTile];  // home tile (box shift applied)
     __shared__ __align__(16) float s_nxyz[3][kTile];  // neighbour tile
     __shared__ float s_hq[kTile], s_nq[kTile];
@@ -333,7 +336,7 @@ k_half_shell(HalfArgs a, BatchArgs b, unsigned long long *sys_pair_count)
             s_hf[0][t] = s_hf[1][t] = s_hf[2][t] = Acc(0);
         }
         __syncthreads();
-        block_boxes(s_hxyz, mh, mh32, s_hbox);
+        block_boxes<W>(s_hxyz, mh, mh32, s_hbox);
         for (int n0 = g.self ? h0 : 0; n0 < nn; n0 += kTile) {
             const int mn = min(kTile, nn - n0);
             const bool diag = g.self && n0 == h0;
@@ -373,7 +376,7 @@ k_half_shell(HalfArgs a, BatchArgs b, unsigned long long *sys_pair_count)
                 for (int t = threadIdx.x; t < (mn32 >> 5) * 6; t += kHT) s_nbox[t / 6][t % 6] = s_hbox[t / 6][t % 6];
                 __syncthreads();
             } else {
-                block_boxes(s_nxyz, mn, mn32, s_nbox);
+                block_boxes<W>(s_nxyz, mn, mn32, s_nbox);
             }
 
             const int nib = mh32 >> 5, njb = mn32 >> 5;
@@ -642,19 +645,35 @@ k_finalize(const void *__restrict__ accum, const int32_t *__restrict__ perm, int
     }
 }
 
-template <int MODE, bool ENERGY, bool MI, bool BATCHED = false>
+template <int MODE, bool ENERGY, bool MI, bool BATCHED = false, int W = kHWDefault,
+          int CAP = KCap<MODE>::value>
 void launch_half_t(const HalfArgs &h, dim3 grid, cudaStream_t stream, const BatchArgs &b = BatchArgs{},
                    unsigned long long *sys_pair_count = nullptr)
 {
     using Acc = typename AccT<MODE>::T;
-    const size_t dyn = sizeof(Acc) * kHW * 3 * KCap<MODE>::value +
-                       sizeof(float2) * (size_t)h.ntypes * (size_t)h.ntypes;
-    static const size_t dyn_max = sizeof(Acc) * kHW * 3 * KCap<MODE>::value +
-                                  sizeof(float2) * kMaxTypes * kMaxTypes;
+    const size_t dyn = sizeof(Acc) * W * 3 * CAP + sizeof(float2) * (size_t)h.ntypes * (size_t)h.ntypes;
+    static const size_t dyn_max = sizeof(Acc) * W * 3 * CAP + sizeof(float2) * kMaxTypes * kMaxTypes;
     static const cudaError_t attr = cudaFuncSetAttribute(
-        k_half_shell<MODE, ENERGY, MI, BATCHED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);
+        k_half_shell<MODE, ENERGY, MI, BATCHED, W, CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        (int)dyn_max);
     (void)attr;
-    k_half_shell<MODE, ENERGY, MI, BATCHED><<<grid, kHT, dyn, stream>>>(h, b, sys_pair_count);
+    k_half_shell<MODE, ENERGY, MI, BATCHED, W, CAP><<<grid, W * 32, dyn, stream>>>(h, b, sys_pair_count);
+}
+
+// The batched launches' kernel shapes (md_batch_tuning): {warps per CTA, survivors
+// buffered per warp} = 0 {4, default}, 1 {2, 256}, 2 {8, 256}, 3 {4, 128}.
+static_assert(MD_BATCH_SHAPES == 4, "one case per shape");
+
+template <int MODE, bool MI>
+void launch_batched_shape(int shape, const HalfArgs &h, dim3 grid, cudaStream_t stream,
+                          const BatchArgs &b, unsigned long long *cnt)
+{
+    switch (shape) {
+    case 1: launch_half_t<MODE, false, MI, true, 2, 256>(h, grid, stream, b, cnt); break;
+    case 2: launch_half_t<MODE, false, MI, true, 8, 256>(h, grid, stream, b, cnt); break;
+    case 3: launch_half_t<MODE, false, MI, true, 4, 128>(h, grid, stream, b, cnt); break;
+    default: launch_half_t<MODE, false, MI, true, 4, KCap<MODE>::value>(h, grid, stream, b, cnt); break;
+    }
 }
 
 }  // namespace
@@ -678,7 +697,7 @@ void cutoff_thresholds(const BoxF &box, double rc, bool mi, float *rc2, float *r
 
 cudaError_t launch_forces_batched(const ForceArgs &a, const BatchArgs &b,
                                   unsigned long long *sys_pair_count, const WsLayout &ws,
-                                  char *wsp, cudaStream_t stream)
+                                  char *wsp, cudaStream_t stream, int shape_reg, int shape_mi)
 {
     Partial *partials = reinterpret_cast<Partial *>(wsp + ws.partials);
     const size_t acc_bytes = (size_t)b.n * (a.mode == MD_ACCUM_FIXED64 ? 24 : 16);
@@ -698,14 +717,14 @@ cudaError_t launch_forces_batched(const ForceArgs &a, const BatchArgs &b,
     if (b.ncell_reg > 0) {
         h.partials = partials;
         dim3 grid(b.ncell_reg, 14);
-        if (a.mode == MD_ACCUM_FIXED64) launch_half_t<MD_ACCUM_FIXED64, false, false, true>(h, grid, stream, b, sys_pair_count);
-        else launch_half_t<MD_ACCUM_F32, false, false, true>(h, grid, stream, b, sys_pair_count);
+        if (a.mode == MD_ACCUM_FIXED64) launch_batched_shape<MD_ACCUM_FIXED64, false>(shape_reg, h, grid, stream, b, sys_pair_count);
+        else launch_batched_shape<MD_ACCUM_F32, false>(shape_reg, h, grid, stream, b, sys_pair_count);
     }
     if (b.ncell_mi > 0) {
         h.partials = partials + (size_t)14 * b.ncell_reg;
         dim3 grid(b.ncell_mi, 27);
-        if (a.mode == MD_ACCUM_FIXED64) launch_half_t<MD_ACCUM_FIXED64, false, true, true>(h, grid, stream, b, sys_pair_count);
-        else launch_half_t<MD_ACCUM_F32, false, true, true>(h, grid, stream, b, sys_pair_count);
+        if (a.mode == MD_ACCUM_FIXED64) launch_batched_shape<MD_ACCUM_FIXED64, true>(shape_mi, h, grid, stream, b, sys_pair_count);
+        else launch_batched_shape<MD_ACCUM_F32, true>(shape_mi, h, grid, stream, b, sys_pair_count);
     }
     const int g = (b.n + 255) / 256;
     if (g > 0) {

@@ -271,7 +271,7 @@ cudaError_t launch_build_cells_batched(const float4 *pos_q, const int32_t *type,
                                        uint32_t *status, cudaStream_t stream);
 cudaError_t launch_forces_batched(const ForceArgs &a, const BatchArgs &b,
                                   unsigned long long *sys_pair_count, const WsLayout &ws,
-                                  char *wsp, cudaStream_t stream);
+                                  char *wsp, cudaStream_t stream, int shape_reg, int shape_mi);
 cudaError_t launch_drift_wrap_batched(double *pos, const double *vel, const float *q, const BatchArgs &b,
                                       double dt, float4 *pos_q_out, uint32_t *status,
                                       cudaStream_t stream);

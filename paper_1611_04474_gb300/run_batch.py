@@ -1,6 +1,7 @@
 """Batched many-system throughput: the systems advanced together through md_batch_step
 (optionally replayed from a captured CUDA graph), against advancing each system alone
-with md_step one after the other on the same GPU.
+with md_step one after the other on the same GPU.  The force launches' kernel shapes
+come from the autotuner (``--tuning auto``, the default), a fixed pair, or the default.
 
     python -m paper_1611_04474_gb300.run_batch --nsys 256 --steps 50 --mode fixed64
 """
@@ -12,6 +13,7 @@ import json
 import torch
 
 from . import api
+from . import autotune
 from . import workloads as W
 
 
@@ -33,6 +35,9 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=4)
     ap.add_argument("--mode", default="fixed64", choices=["f32", "fixed64"])
     ap.add_argument("--no-alone", action="store_true")
+    ap.add_argument("--tuning", default="auto",
+                    help="'auto' (autotuner with its cache), 'retune', or two shapes 'r,s'")
+    ap.add_argument("--cache", default=autotune.DEFAULT_CACHE)
     args = ap.parse_args(argv)
     mode = api.ACCUM_F32 if args.mode == "f32" else api.ACCUM_FIXED64
     systems = W.batch_of_systems(nsys=args.nsys, seed=args.seed)
@@ -40,6 +45,12 @@ def main(argv=None):
            "mode": args.mode, "rc_clamped": sum(bool(s.meta["rc_clamped"]) for s in systems)}
 
     b = api.Batch(systems, mode=mode)
+    if args.tuning in ("auto", "retune"):
+        tuned = autotune.tune(b, cache_path=args.cache, retune=args.tuning == "retune")
+        out["autotune"] = {k: tuned[k] for k in ("key", "tuning", "measured", "ms") if k in tuned}
+    else:
+        b.tuning = tuple(int(v) for v in args.tuning.split(","))
+    out["tuning"] = list(b.tuning)
     b.step(1, count_pairs=True)  # forces of the start state + one step, outside timing
     torch.cuda.synchronize()
     b.pair_count.zero_()

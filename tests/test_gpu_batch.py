@@ -70,3 +70,53 @@ def test_f32_batch_matches_oracle(cuda_lib):
         alts, nb = boundary_alternatives(p, s, ff, ref.F)
         err = force_errors(F[b.system_slice(k)], ref.F, ref.cond, alts)
         assert err["max_norm"] <= 1e-5, (k, err)
+
+
+@pytest.mark.parametrize("mode", ["fixed64", "f32"])
+def test_every_kernel_shape_gives_the_same_result(cuda_lib, mode):
+    """The tuning shapes change only the launch: FIXED64 forces and trajectories are the
+    same bits and the pair counts are equal under every shape; F32 agrees to rounding."""
+    api = cuda_lib
+    m = api.ACCUM_FIXED64 if mode == "fixed64" else api.ACCUM_F32
+    systems = _systems()
+    ref = None
+    for r in range(api.BATCH_SHAPES):
+        for s in range(api.BATCH_SHAPES):
+            if r and s and r != s:
+                continue  # each shape in each regime, against the default in the other
+            b = api.Batch(systems, mode=m, tuning=(r, s))
+            # F32 trajectories differ by rounding between shapes: compare start forces
+            b.step(2 if m == api.ACCUM_FIXED64 else 0, dt_fs=1.0, count_pairs=True)
+            torch.cuda.synchronize()
+            assert int(b.status.item()) == 0, (r, s)
+            got = (b.forces.cpu().numpy(), b.pos.cpu().numpy(), b.pair_count.cpu().numpy())
+            if ref is None:
+                ref = got
+                continue
+            assert np.array_equal(got[2], ref[2]), (r, s)
+            if m == api.ACCUM_FIXED64:
+                assert np.array_equal(got[0], ref[0]), (r, s)
+                assert np.array_equal(got[1], ref[1]), (r, s)
+            else:
+                scale = np.abs(ref[0]).max()
+                assert np.abs(got[0].astype(np.float64) - ref[0]).max() <= 1e-5 * scale, (r, s)
+
+
+def test_autotuner_leaves_the_trajectory_and_caches(cuda_lib, tmp_path):
+    api = cuda_lib
+    from paper_1611_04474_gb300 import autotune
+
+    systems = _systems()
+    plain = api.Batch(systems, mode=api.ACCUM_FIXED64)
+    plain.step(3, dt_fs=1.0)
+    tuned = api.Batch(systems, mode=api.ACCUM_FIXED64)
+    cache = str(tmp_path / "tuning.json")
+    e1 = autotune.tune(tuned, cache_path=cache, n_steps=1, reps=1)
+    assert e1["measured"] and len(e1["ms"]) == 2  # both regimes are present
+    tuned.step(3, dt_fs=1.0)
+    torch.cuda.synchronize()
+    assert np.array_equal(tuned.pos.cpu().numpy(), plain.pos.cpu().numpy())
+    assert np.array_equal(tuned.forces.cpu().numpy(), plain.forces.cpu().numpy())
+    again = api.Batch(systems, mode=api.ACCUM_FIXED64)
+    e2 = autotune.tune(again, cache_path=cache)
+    assert not e2["measured"] and tuple(e2["tuning"]) == tuple(e1["tuning"]) == again.tuning
