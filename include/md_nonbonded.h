@@ -67,10 +67,15 @@ extern "C" {
 #define MD_ACCUM_F64 2     /* FP64 pair math and accumulation, a slow reference mode;
                               forces double[n][3] */
 
-/* force-kernel choice for md_nonbonded_forces_algo (md_nonbonded_forces picks the default) */
+/* force-kernel choice for md_nonbonded_forces_algo.  MD_ALGO_DEFAULT (what
+ * md_nonbonded_forces and md_step use): MD_ALGO_CLUSTER for MD_ACCUM_F32 and
+ * MD_ACCUM_FIXED64, MD_ALGO_FULL_SHELL for MD_ACCUM_F64 (its only kernel). */
 #define MD_ALGO_DEFAULT 0
 #define MD_ALGO_FULL_SHELL 1 /* one thread per home atom over all 27 neighbour cells (Alg. 1) */
 #define MD_ALGO_HALF_SHELL 2 /* each cell pair once, reactions by Newton's third law */
+#define MD_ALGO_CLUSTER 3    /* the half shell filtered by clusters of 4 x 8 atoms, every pair of
+                                a cluster pair in range evaluated; boxes with an axis of 2
+                                cells run MD_ALGO_HALF_SHELL */
 
 /* Force-field constants of Eq. 1-2.  Host struct; AB is a DEVICE pointer to
  * float[ntypes][ntypes][2] holding (A_ij, B_ij) of Eq. 1 (symmetric in i,j). */

@@ -23,6 +23,7 @@ ACCUM_F64 = 2
 ALGO_DEFAULT = 0
 ALGO_FULL_SHELL = 1
 ALGO_HALF_SHELL = 2
+ALGO_CLUSTER = 3
 STATUS_NONFINITE = 1
 STATUS_FIXED_OVERFLOW = 2
 STATUS_BAD_TYPE = 4

@@ -119,6 +119,9 @@ WsLayout ws_layout(int n, int ncell)
     w.st_pos_q_sorted = off; off = align_up(off + sizeof(float4) * nn);
     w.st_type_sorted = off;  off = align_up(off + sizeof(int32_t) * nn);
     w.st_pos_q = off;        off = align_up(off + sizeof(float4) * nn);
+    w.clu_pos_q = off;       off = align_up(off + sizeof(float4) * nn);
+    w.clu_type = off;        off = align_up(off + sizeof(int32_t) * nn);
+    w.clu_order = off;       off = align_up(off + sizeof(int32_t) * nn);
     w.total = off;
     return w;
 }
@@ -228,7 +231,8 @@ int md_nonbonded_forces_algo(const int32_t *cell_start, const int32_t *perm,
     int e = check_ff(ff);
     if (e) return e;
     if (mode != MD_ACCUM_F32 && mode != MD_ACCUM_FIXED64 && mode != MD_ACCUM_F64) return MD_ERR_INVALID_ARG;
-    if (algo != MD_ALGO_DEFAULT && algo != MD_ALGO_FULL_SHELL && algo != MD_ALGO_HALF_SHELL)
+    if (algo != MD_ALGO_DEFAULT && algo != MD_ALGO_FULL_SHELL && algo != MD_ALGO_HALF_SHELL &&
+        algo != MD_ALGO_CLUSTER)
         return MD_ERR_INVALID_ARG;
     int32_t want[3];
     if ((e = compute_dims(box_L, ff->rc, want))) return e;

@@ -209,9 +209,13 @@ cudaError_t launch_forces(const ForceArgs &a, const WsLayout &ws, char *wsp, cud
     // the FP64 reference mode always runs the full-shell kernel
     int algo = a.algo;
     if (algo == MD_ALGO_DEFAULT || a.mode == MD_ACCUM_F64)
-        algo = a.mode == MD_ACCUM_F64 ? MD_ALGO_FULL_SHELL : MD_ALGO_HALF_SHELL;
+        algo = a.mode == MD_ACCUM_F64 ? MD_ALGO_FULL_SHELL : MD_ALGO_CLUSTER;
+    if (algo == MD_ALGO_CLUSTER && !cluster_kernel_applies(a.box)) algo = MD_ALGO_HALF_SHELL;
     int nblocks = a.box.ncell;
-    if (algo == MD_ALGO_HALF_SHELL) {
+    if (algo == MD_ALGO_CLUSTER) {
+        cudaError_t e = launch_cluster(a, ws, wsp, partials, &nblocks, stream);
+        if (e != cudaSuccess) return e;
+    } else if (algo == MD_ALGO_HALF_SHELL) {
         cudaError_t e = launch_half_shell(a, ws, wsp, partials, &nblocks, stream);
         if (e != cudaSuccess) return e;
     } else {

@@ -60,6 +60,7 @@ struct WsLayout {
     size_t partials;    // Partial [nslots]
     size_t ev;          // double[4]          energy/virial scratch of md_step
     size_t st_cell_start, st_perm, st_pos_q_sorted, st_type_sorted, st_pos_q;  // md_step only
+    size_t clu_pos_q, clu_type, clu_order;  // cluster-pair kernel: per-cell reordered copies
     size_t total;
     int nslots;
 };
@@ -255,6 +256,9 @@ int half_shell_pairs_per_cell(const BoxF &box);
 void cutoff_thresholds(const BoxF &box, double rc, bool mi, float *rc2, float *rc2m);
 cudaError_t launch_half_shell(const ForceArgs &a, const WsLayout &ws, char *wsp, Partial *partials,
                               int *nblocks_out, cudaStream_t stream);
+bool cluster_kernel_applies(const BoxF &box);
+cudaError_t launch_cluster(const ForceArgs &a, const WsLayout &ws, char *wsp, Partial *partials,
+                           int *nblocks_out, cudaStream_t stream);
 
 // Batched forms: every system of the batch in one launch per kernel.
 struct BatchArgs {

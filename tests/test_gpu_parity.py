@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 TOL_F32 = 1e-5
 TOL_F64 = 1e-12
 
-ALGOS_F32 = [1, 2]  # full shell, half shell
+ALGOS_F32 = [1, 2, 3]  # full shell, half shell, cluster pairs
 
 SYSTEMS = {
     "gas3000": lambda: W.workload_random_3000(),
@@ -99,7 +99,7 @@ def test_fixed_mode_exact_sum_and_reproducible(cuda_lib, name):
     api = cuda_lib
     s, ff, p, ref, alts, nb = ref_for(name)
     runs = []
-    for algo in (1, 2, 2, 2):
+    for algo in (1, 2, 3, 2, 3):
         eng = run_forces(api, s, api.ACCUM_FIXED64, algo)
         runs.append(eng.forces.cpu().numpy().copy())
     # the same integers from both kernels and from run to run
@@ -109,14 +109,15 @@ def test_fixed_mode_exact_sum_and_reproducible(cuda_lib, name):
     assert np.all(runs[0].sum(axis=0, dtype=np.int64) == 0)
 
 
-def test_fixed_mode_permutation_invariant(cuda_lib):
+@pytest.mark.parametrize("algo", [2, 3])
+def test_fixed_mode_permutation_invariant(cuda_lib, algo):
     api = cuda_lib
     s = SYSTEMS["box_5x5x7_ragged"]()
-    base = run_forces(api, s, api.ACCUM_FIXED64, 2).forces.cpu().numpy()
+    base = run_forces(api, s, api.ACCUM_FIXED64, algo).forces.cpu().numpy()
     perm = np.random.default_rng(1).permutation(s.n)
     s2 = W.System(s.name, s.pos[perm], s.q[perm], s.type[perm], s.box, s.rc, s.sigma, s.eps, s.AB,
                   s.mass[perm], s.vel[perm])
-    got = run_forces(api, s2, api.ACCUM_FIXED64, 2).forces.cpu().numpy()
+    got = run_forces(api, s2, api.ACCUM_FIXED64, algo).forces.cpu().numpy()
     assert np.array_equal(got, base[perm])
 
 
@@ -221,6 +222,31 @@ def test_atoms_on_cell_boundaries_and_outside_the_box(cuda_lib):
     ff, p, ref, alts, nb = _oracle_ref(s_in)
     err = force_errors(eng.forces.cpu().numpy(), ref.F, ref.cond, alts)
     assert err["max_norm"] <= TOL_F64
+
+
+def test_crowded_cells(cuda_lib):
+    """Cells of more than one staged tile (512 atoms) and one cell beyond the cluster
+    ordering's limit (1,331 atoms, kept in sorted order), against the oracle; FIXED64
+    the same bits from every kernel."""
+    api = cuda_lib
+    g = np.stack(np.meshgrid(*[np.arange(24)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    rng = np.random.default_rng(11)
+    dense = _custom(0.25 + 0.5 * g + rng.uniform(-0.03, 0.03, g.shape), (12.0, 12.0, 12.0), rc=4.0)
+    b = np.stack(np.meshgrid(*[np.arange(11)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    blob = 0.2 + 0.33 * b + rng.uniform(-0.02, 0.02, b.shape)       # one cell, 1,331 atoms
+    rest = rng.uniform((5.5, 0.0, 0.0), (12.0, 12.0, 12.0), (300, 3))  # away from the blob
+    keep = np.ones(len(rest), bool)
+    for k in range(len(rest)):  # at least 0.8 A apart
+        d = np.linalg.norm(rest[:k][keep[:k]] - rest[k], axis=1)
+        keep[k] = not np.any(d < 0.8)
+    mixed = _custom(np.concatenate([blob, rest[keep]]), (12.0, 12.0, 12.0), rc=4.0)
+    for s, least in ((dense, 257), (mixed, 1025)):
+        c3 = np.minimum(np.floor(s.pos.astype(np.float64) / 4.0), 2).astype(int)
+        counts = np.bincount(c3[:, 0] + 3 * (c3[:, 1] + 3 * c3[:, 2]), minlength=27)
+        assert counts.max() >= least
+        _check_vs_oracle(api, s, modes=(0, 1))
+        fx = [run_forces(api, s, api.ACCUM_FIXED64, algo).forces.cpu().numpy() for algo in (1, 2, 3)]
+        assert np.array_equal(fx[0], fx[1]) and np.array_equal(fx[0], fx[2])
 
 
 def test_many_types(cuda_lib):
