@@ -38,13 +38,12 @@ FLOP_PER_CANDIDATE = 8
 FLOP_PER_PAIR = 22
 
 
-# DRAM bytes of one md_nonbonded_forces launch (dram__bytes_read.sum + dram__bytes_write.sum
-# of k_half_shell, 92,224-atom lattice) from the ncu capture summarised in
-# profiles/k_half_shell_lattice92k.md, with the SHA-256 of the kernel source it was taken
-# on: the figure is reported as null once that source has changed.
-TRAFFIC_CAPTURE = {"bytes": 3369472, "atoms": 92224,
-                   "kernel_source_sha256": "9d05ca718db861b8029cb1506507be15a7b3aae6a246cc7b0065ee496550de0b"}
-KERNEL_SOURCE = os.path.join(ROOT, "paper_1611_04474_gb300", "csrc", "md_forces_half.cu")
+# DRAM bytes of one launch of the dominant kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum of k_cluster, 92,224-atom lattice) from the ncu capture summarised
+# under profiles/, with the SHA-256 of the kernel source it was taken on: the figure is
+# reported as null once that source has changed.
+TRAFFIC_CAPTURE = {"bytes": None, "atoms": 92224, "kernel_source_sha256": None}
+KERNEL_SOURCE = os.path.join(ROOT, "paper_1611_04474_gb300", "csrc", "md_forces_cluster.cu")
 
 
 def captured_traffic(n_atoms: int):
@@ -69,6 +68,7 @@ def parse():
     ap.add_argument("--n", type=int, default=92224, help="atoms (lattice at ApoA1 density)")
     ap.add_argument("--mode", default="f32", choices=["f32", "fixed64"])
     ap.add_argument("--algo", type=int, default=0)
+    ap.add_argument("--no-energy", action="store_true", help="skip the board-energy run")
     ap.add_argument("--dt", type=float, default=1.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -157,6 +157,70 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def measure_energy(eng, stream, dev_index: int, seconds: float = 2.0, dt_fs: float = 0.01):
+    """Board energy per MD step: a sustained run of steps (about `seconds`) with
+    nvidia-smi sampling power.draw every 50 ms; J/step = mean power over the run x the
+    event-timed time per step.  The run starts from a copy of the current state with a
+    short time step (the cost of a step does not depend on dt) and the state is restored
+    afterwards, so the trajectory of the timed steps is not changed."""
+    import datetime
+
+    import torch
+
+    saved = {k: getattr(eng, k).clone() for k in ("pos", "vel", "forces", "pos_q")}
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    eng.step(20, dt_fs=dt_fs)
+    b.record(stream)
+    torch.cuda.synchronize()
+    n_steps = max(100, int(seconds * 1e3 / (a.elapsed_time(b) / 20)))
+    path = os.path.join(ROOT, "gpurun_out", f"power_gpu{dev_index}.csv")
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        f = open(path, "w")
+        proc = subprocess.Popen(["nvidia-smi", "-i", str(dev_index), "--query-gpu=timestamp,power.draw",
+                                 "--format=csv,noheader,nounits", "-lms", "50"],
+                                stdout=f, stderr=subprocess.DEVNULL)
+    except (OSError, FileNotFoundError):
+        return None
+    time.sleep(0.5)
+    torch.cuda.synchronize()
+    t0 = datetime.datetime.now()
+    a.record(stream)
+    eng.step(n_steps, dt_fs=dt_fs)
+    b.record(stream)
+    torch.cuda.synchronize()
+    t1 = datetime.datetime.now()
+    time.sleep(0.2)
+    proc.terminate()
+    try:
+        proc.wait(timeout=5)
+    except subprocess.TimeoutExpired:
+        proc.kill()
+    f.close()
+    for k, v in saved.items():
+        getattr(eng, k).copy_(v)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    watts = []
+    for line in open(path):
+        parts = [x.strip() for x in line.split(",")]
+        try:
+            ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f")
+            w = float(parts[1])
+        except (ValueError, IndexError):
+            continue
+        if t0 <= ts <= t1:
+            watts.append(w)
+    if len(watts) < 5:
+        return None
+    p_mean = statistics.mean(watts)
+    return {"joules_per_step": p_mean * ms / 1e3 / n_steps, "mean_power_w": p_mean,
+            "ms_per_step": ms / n_steps, "steps": n_steps, "samples": len(watts),
+            "dt_fs": dt_fs, "source": "nvidia-smi power.draw, 50 ms samples within the run"}
 
 
 def combine_ranks(pairs: float, step_ms: float, e2e_ms: float, device=None):
@@ -311,6 +375,7 @@ def run_ours(args):
     pairs_end = int(eng.pair_count.item())
     status = int(eng.status.item())
     clk = clocks.stop()
+    energy = None if args.no_energy else measure_energy(eng, stream, dev.index)
 
     # end to end through the public API with host buffers: pinned state in, result out
     pos_h = eng.pos.cpu().pin_memory()
@@ -344,11 +409,14 @@ def run_ours(args):
     value = total_pairs / (t_step / 1e3)
     e2e_value = total_pairs / (t_e2e / 1e3)
 
+    if energy:
+        energy["pairs_per_joule"] = pairs_per_step / energy["joules_per_step"]
     flops = FLOP_PER_CANDIDATE * candidates + FLOP_PER_PAIR * pairs_end
     sm_clock_ghz = 2.07
     peak_tflops = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_clock_ghz / 1e3
     achieved = flops / (t_force / 1e3) / 1e12
-    per_step_launches = 8  # kick, drift+wrap, 4 cell-build kernels, forces, kick
+    # kick, drift+wrap, 4 cell-build kernels, cluster order, force kernel, finalize, kick
+    per_step_launches = 10 if args.algo in (0, 3) else 9
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step / args.steps, "higher_is_better": True,
@@ -370,7 +438,8 @@ def run_ours(args):
                      "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz (derived)"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": args.steps * per_step_launches + args.steps,
+        "gpu_launches": args.steps * per_step_launches,
+        "energy": energy,
         "clocks": clk,
         "status": status,
     }

@@ -8,22 +8,27 @@
 //
 //   order:   each cell's atoms are reordered into spatially compact groups: columns
 //            of an S x S grid over the cell's x-y face, each column sorted along z
-//            (alternating direction), so that consecutive atoms are neighbours.  A
-//            home cell is cut into i-clusters of 4 atoms, a neighbour cell into
-//            j-clusters of 8.
-//   filter:  one lane per j-cluster tests the gap between the bounding boxes of the
-//            i-cluster and 32 j-clusters at once (rc'^2, conservative); a ballot
-//            lists the j-clusters in range (about 39% of their 32 pairs are within
-//            rc on the dense workloads, against 14% of the cell-pair candidates).
-//   force:   a warp evaluates the 4 x 8 pairs of one cluster pair, one pair per lane
-//            (lane = i + 4 j), with the exact test r^2 < rc^2 per pair.
-//   reduce:  i-forces stay in registers for the whole i-cluster; the reaction on each
-//            j atom is summed over its 4 lanes with two shuffles and added to a
-//            warp-private shared array (no atomics inside a tile).
+//            (alternating direction), so that consecutive atoms are neighbours.  Every
+//            8 consecutive atoms of a cell form a cluster.
+//   filter:  one lane per neighbour cluster tests the gap between the bounding boxes
+//            of a home cluster and 32 neighbour clusters at once (rc'^2, conservative);
+//            a ballot lists the clusters in range (about 37% of their 64 pairs lie
+//            within rc on the dense workloads, against 14% of the cell-pair
+//            candidates).
+//   force:   a warp evaluates the 8 x 8 pairs of one cluster pair: lane i + 4 j holds
+//            home atoms i and i + 4 and neighbour atom j and evaluates those two pairs,
+//            with the exact test r^2 < rc^2 per pair.  MD_ACCUM_F32 evaluates them
+//            with packed FP32x2 instructions (Blackwell's paired FP32 ALU);
+//            MD_ACCUM_FIXED64 with the library's scalar pair_r2 / pair_f on the same
+//            staged coordinates and shifts as the half-shell kernel, so its integers
+//            are the same bits as the other kernels' (the compiler may contract packed
+//            multiply-adds, which would move a pair force by an ulp).
+//   reduce:  home-atom forces stay in registers for the whole home cluster; the
+//            reaction on each neighbour atom is summed over its two pairs, then over
+//            its 4 lanes by two shuffles, and added to a warp-private shared array
+//            (F32) or with one integer shared atomic per component (FIXED64).
 //
-// The pair arithmetic is the library's (pair_r2, pair_f, the same staged coordinates
-// and shifts as the half-shell kernel), so MD_ACCUM_FIXED64 results are the same bits
-// as the other kernels'.  Boxes with an axis of 2 cells use the half-shell kernel.
+// Boxes with an axis of 2 cells use the half-shell kernel.
 #include <math.h>
 
 #include "md_internal.cuh"
@@ -32,17 +37,14 @@
 namespace mdnb {
 namespace {
 
-constexpr int kCI = 4;         // atoms per i-cluster (home cell)
-constexpr int kCJ = 8;         // atoms per j-cluster (neighbour cell)
-constexpr int kCW = 4;         // warps per CTA
-constexpr int kCT = kCW * 32;  // threads per CTA
-constexpr int kCTile = 256;    // atoms of a cell staged at once (multiple of kCJ)
-constexpr int kSortMax = 1024; // cells with more atoms keep their sorted order
+constexpr int kCS = 8;          // atoms per cluster
+constexpr int kCW = 4;          // warps per CTA
+constexpr int kCT = kCW * 32;   // threads per CTA
+constexpr int kCTile = 256;     // atoms of a cell staged at once (whole clusters)
+constexpr int kSortMax = 1024;  // cells with more atoms keep their sorted order
 constexpr int kOrderThreads = 256;
 
-static_assert(kCI * kCJ == 32, "one cluster pair per warp");
-static_assert(kCTile % kCJ == 0 && kCTile % kCI == 0, "tiles hold whole clusters");
-
+static_assert(kCTile % kCS == 0 && kCTile / kCS <= 32, "a tile's clusters fit one ballot");
 // Per cell: sort its atoms by (column, z along the column) and write the reordered
 // copies.  corder[k] is the sorted-order slot of cluster-order slot k.
 __global__ void __launch_bounds__(kOrderThreads)
@@ -90,6 +92,32 @@ k_cluster_order(const int32_t *__restrict__ cell_start, const float4 *__restrict
     }
 }
 
+// Packed pairs of FP32 values (element 0 in the low half).
+typedef unsigned long long f2;
+
+__device__ __forceinline__ f2 f2_make(float lo, float hi)
+{
+    f2 d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+    return d;
+}
+__device__ __forceinline__ void f2_split(f2 v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b)
+{
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b)
+{
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 struct CluArgs {
     const int32_t *cell_start;
     const float4 *pq;   // cluster order
@@ -107,14 +135,13 @@ struct CluArgs {
 };
 
 // Bounding boxes of the clusters of a staged tile (padding excluded).
-template <int CS>
 __device__ __forceinline__ void cluster_boxes(const float4 *p, int m, float (*box)[6])
 {
-    const int nclu = (m + CS - 1) / CS;
+    const int nclu = (m + kCS - 1) / kCS;
     for (int k = threadIdx.x; k < nclu; k += kCT) {
         float lo[3] = {kFar, kFar, kFar}, hi[3] = {-kFar, -kFar, -kFar};
-        const int e = min(m, (k + 1) * CS);
-        for (int t = k * CS; t < e; ++t) {
+        const int e = min(m, (k + 1) * kCS);
+        for (int t = k * kCS; t < e; ++t) {
             const float4 q = p[t];
             lo[0] = fminf(lo[0], q.x); hi[0] = fmaxf(hi[0], q.x);
             lo[1] = fminf(lo[1], q.y); hi[1] = fmaxf(hi[1], q.y);
@@ -128,25 +155,256 @@ __device__ __forceinline__ void cluster_boxes(const float4 *p, int m, float (*bo
     }
 }
 
+// Shared tiles of one CTA.  Reactions: F32 one array per warp (plain read-modify-write,
+// no float atomics); FIXED64 one array for the CTA (native integer shared atomics).
+template <int MODE>
+struct CluSmem {
+    using Acc = typename AccT<MODE>::T;
+    static constexpr int NW = MODE == MD_ACCUM_FIXED64 ? 1 : kCW;
+    float4 hp[kCTile];  // home tile (x, y, z shifted, q)
+    float4 np[kCTile];  // neighbour tile
+    int ht[kCTile], nt[kCTile];
+    float ib[kCTile / kCS][6];  // home cluster boxes: lo xyz, hi xyz
+    float jb[kCTile / kCS][6];  // neighbour cluster boxes
+    Acc hf[3][kCTile];          // forces on home atoms (whole cell pair)
+    Acc nf[NW][3][kCTile];      // reactions on neighbour atoms (this tile)
+};
+
+struct CluConst {
+    float kc, rc2, rc2m;
+    float lo[3];
+    int T;
+    uint32_t *status;
+};
+
+// Home cluster ic against every neighbour cluster of the staged tile in range.
+// DIAG: the neighbour tile is the home tile (pairs ia < ja only); SHIFT: the cell
+// pair has a remainder shift to add to the difference.
+template <int MODE, bool ENERGY, bool DIAG, bool SHIFT>
+__device__ __forceinline__ void cluster_row(CluSmem<MODE> &sm, const float2 *s_ab,
+                                            const CluConst &k, int ic, int njc, int mh, int warp,
+                                            int lane, float &e_lj, float &e_c, float &vir,
+                                            unsigned &cnt)
+{
+    using Acc = typename AccT<MODE>::T;
+    const int il = lane & 3, jl = lane >> 2;
+    const int ia0 = ic * kCS + il, ia1 = ia0 + 4;
+    const float4 p0 = sm.hp[ia0], p1 = sm.hp[ia1];
+    const f2 xi = f2_make(p0.x, p1.x), yi = f2_make(p0.y, p1.y), zi = f2_make(p0.z, p1.z);
+    const f2 qi = f2_make(p0.w, p1.w);
+    const int t0 = sm.ht[ia0] * k.T, t1 = sm.ht[ia1] * k.T;
+    const f2 kc2 = f2_make(k.kc, k.kc), m05 = f2_make(-0.5f, -0.5f), c15 = f2_make(1.5f, 1.5f);
+    const f2 lox = f2_make(k.lo[0], k.lo[0]), loy = f2_make(k.lo[1], k.lo[1]),
+             loz = f2_make(k.lo[2], k.lo[2]);
+    float ib[6];
+#pragma unroll
+    for (int d = 0; d < 6; ++d) ib[d] = sm.ib[ic][d];
+    // home-atom sums: F32 packed (atom ia0 low, ia1 high); FIXED64 one integer each
+    f2 ax2 = 0ull, ay2 = 0ull, az2 = 0ull;
+    Acc ax0 = Acc(0), ay0 = Acc(0), az0 = Acc(0), ax1 = Acc(0), ay1 = Acc(0), az1 = Acc(0);
+
+    const int jc0 = DIAG ? ic : 0;
+    for (int jb = jc0; jb < njc; jb += 32) {
+        const int jt = jb + lane;
+        bool in = false;
+        if (jt < njc) {
+            const float *q = sm.jb[jt];
+            const float gx = fmaxf(0.f, fmaxf(ib[0] - q[3], q[0] - ib[3]));
+            const float gy = fmaxf(0.f, fmaxf(ib[1] - q[4], q[1] - ib[4]));
+            const float gz = fmaxf(0.f, fmaxf(ib[2] - q[5], q[2] - ib[5]));
+            in = gx * gx + gy * gy + gz * gz < k.rc2m;
+        }
+        unsigned todo = __ballot_sync(0xffffffffu, in);
+        while (todo) {
+            const int jc = jb + __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int ja = jc * kCS + jl;
+            const float4 pj = sm.np[ja];
+            const int tj = sm.nt[ja];
+            const float2 ab0 = s_ab[t0 + tj], ab1 = s_ab[t1 + tj];  // (A, -B)
+            Acc vx, vy, vz;  // reaction on ja (before the sign): this lane's two pairs
+            if (MODE == MD_ACCUM_FIXED64) {
+                // the library's scalar pair arithmetic, pair by pair
+                float d0[3] = {p0.x - pj.x, p0.y - pj.y, p0.z - pj.z};
+                float d1[3] = {p1.x - pj.x, p1.y - pj.y, p1.z - pj.z};
+                if (SHIFT) {
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        d0[d] = d0[d] + k.lo[d];
+                        d1[d] = d1[d] + k.lo[d];
+                    }
+                }
+                const float r20 = pair_r2(d0[0], d0[1], d0[2]), r21 = pair_r2(d1[0], d1[1], d1[2]);
+                // padding sits at +-1e18: such pairs fail the cutoff test
+                const bool ok0 = r20 < k.rc2 && (!DIAG || ia0 < ja);
+                const bool ok1 = r21 < k.rc2 && (!DIAG || ia1 < ja);
+                const float kqq0 = __fmul_rn(k.kc, __fmul_rn(p0.w, pj.w));
+                const float kqq1 = __fmul_rn(k.kc, __fmul_rn(p1.w, pj.w));
+                float ir0, ir20, ir60, ir1, ir21, ir61;
+                float f0 = pair_f(r20, ab0.x, -ab0.y, kqq0, ir0, ir20, ir60);
+                float f1 = pair_f(r21, ab1.x, -ab1.y, kqq1, ir1, ir21, ir61);
+                f0 = ok0 ? f0 : 0.0f;
+                f1 = ok1 ? f1 : 0.0f;
+                Acc g0[3], g1[3];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    g0[d] = (Acc)(ok0 ? to_fixed(__fmul_rn(f0, d0[d]), k.status) : 0);
+                    g1[d] = (Acc)(ok1 ? to_fixed(__fmul_rn(f1, d1[d]), k.status) : 0);
+                }
+                ax0 += g0[0]; ay0 += g0[1]; az0 += g0[2];
+                ax1 += g1[0]; ay1 += g1[1]; az1 += g1[2];
+                vx = g0[0] + g1[0];
+                vy = g0[1] + g1[1];
+                vz = g0[2] + g1[2];
+                cnt += (unsigned)ok0 + (unsigned)ok1;
+                if (ENERGY) {
+                    if (ok0) {
+                        e_lj += pair_u_lj(ab0.x, -ab0.y, ir60);
+                        e_c += kqq0 * ir0;
+                        vir += f0 * r20;
+                    }
+                    if (ok1) {
+                        e_lj += pair_u_lj(ab1.x, -ab1.y, ir61);
+                        e_c += kqq1 * ir1;
+                        vir += f1 * r21;
+                    }
+                }
+            } else {
+                f2 dx = f2_sub(xi, f2_dup(pj.x)), dy = f2_sub(yi, f2_dup(pj.y)), dz = f2_sub(zi, f2_dup(pj.z));
+                if (SHIFT) {
+                    dx = f2_add(dx, lox);
+                    dy = f2_add(dy, loy);
+                    dz = f2_add(dz, loz);
+                }
+                const f2 r2 = f2_fma(dz, dz, f2_fma(dy, dy, f2_mul(dx, dx)));
+                float r20, r21;
+                f2_split(r2, r20, r21);
+                // padding sits at +-1e18: such pairs fail the cutoff test
+                const bool ok0 = r20 < k.rc2 && (!DIAG || ia0 < ja);
+                const bool ok1 = r21 < k.rc2 && (!DIAG || ia1 < ja);
+                const f2 A2 = f2_make(ab0.x, ab1.x), nB2 = f2_make(ab0.y, ab1.y);
+                const f2 kqq = f2_mul(kc2, f2_mul(qi, f2_dup(pj.w)));
+                // pair_f, element by element: rsqrt_nr, the powers, Eq. 1 + Eq. 2
+                float y0, y1;
+                asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(r20));
+                asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y1) : "f"(r21));
+                const f2 y = f2_make(y0, y1);
+                const f2 ir = f2_mul(y, f2_fma(f2_mul(m05, r2), f2_mul(y, y), c15));
+                const f2 ir2 = f2_mul(ir, ir);
+                const f2 ir6 = f2_mul(f2_mul(ir2, ir2), ir2);
+                const f2 ir8 = f2_mul(ir6, ir2);
+                const f2 lj = f2_fma(A2, f2_mul(ir8, ir6), f2_mul(nB2, ir8));
+                const f2 cl = f2_mul(f2_mul(kqq, ir2), ir);
+                float f0, f1;
+                f2_split(f2_add(lj, cl), f0, f1);
+                f0 = ok0 ? f0 : 0.0f;
+                f1 = ok1 ? f1 : 0.0f;
+                const f2 f = f2_make(f0, f1);
+                const f2 fx = f2_mul(f, dx), fy = f2_mul(f, dy), fz = f2_mul(f, dz);
+                ax2 = f2_add(ax2, fx);
+                ay2 = f2_add(ay2, fy);
+                az2 = f2_add(az2, fz);
+                float a0, a1;
+                f2_split(fx, a0, a1);
+                vx = (Acc)(a0 + a1);
+                f2_split(fy, a0, a1);
+                vy = (Acc)(a0 + a1);
+                f2_split(fz, a0, a1);
+                vz = (Acc)(a0 + a1);
+                cnt += (unsigned)ok0 + (unsigned)ok1;
+                if (ENERGY) {
+                    float i6a, i6b, ira, irb, ka, kb;
+                    f2_split(ir6, i6a, i6b);
+                    f2_split(ir, ira, irb);
+                    f2_split(kqq, ka, kb);
+                    if (ok0) {
+                        e_lj += pair_u_lj(ab0.x, -ab0.y, i6a);
+                        e_c += ka * ira;
+                        vir += f0 * r20;
+                    }
+                    if (ok1) {
+                        e_lj += pair_u_lj(ab1.x, -ab1.y, i6b);
+                        e_c += kb * irb;
+                        vir += f1 * r21;
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = 1; o < 4; o <<= 1) {
+                vx += __shfl_xor_sync(0xffffffffu, vx, o);
+                vy += __shfl_xor_sync(0xffffffffu, vy, o);
+                vz += __shfl_xor_sync(0xffffffffu, vz, o);
+            }
+            if (il == 0) {
+                if (MODE == MD_ACCUM_FIXED64) {
+                    atomicAdd(reinterpret_cast<unsigned long long *>(&sm.nf[0][0][ja]), (unsigned long long)(Acc(0) - vx));
+                    atomicAdd(reinterpret_cast<unsigned long long *>(&sm.nf[0][1][ja]), (unsigned long long)(Acc(0) - vy));
+                    atomicAdd(reinterpret_cast<unsigned long long *>(&sm.nf[0][2][ja]), (unsigned long long)(Acc(0) - vz));
+                } else {
+                    Acc(*nf)[kCTile] = sm.nf[MODE == MD_ACCUM_FIXED64 ? 0 : warp];
+                    nf[0][ja] -= vx;
+                    nf[1][ja] -= vy;
+                    nf[2][ja] -= vz;
+                }
+            }
+        }
+    }
+    // home-atom sums over the 8 lanes that share them; the home cluster belongs to
+    // this warp alone within the CTA
+    if (MODE == MD_ACCUM_FIXED64) {
+#pragma unroll
+        for (int o = 4; o < 32; o <<= 1) {
+            ax0 += __shfl_xor_sync(0xffffffffu, ax0, o);
+            ay0 += __shfl_xor_sync(0xffffffffu, ay0, o);
+            az0 += __shfl_xor_sync(0xffffffffu, az0, o);
+            ax1 += __shfl_xor_sync(0xffffffffu, ax1, o);
+            ay1 += __shfl_xor_sync(0xffffffffu, ay1, o);
+            az1 += __shfl_xor_sync(0xffffffffu, az1, o);
+        }
+    } else {
+#pragma unroll
+        for (int o = 4; o < 32; o <<= 1) {
+            ax2 = f2_add(ax2, __shfl_xor_sync(0xffffffffu, ax2, o));
+            ay2 = f2_add(ay2, __shfl_xor_sync(0xffffffffu, ay2, o));
+            az2 = f2_add(az2, __shfl_xor_sync(0xffffffffu, az2, o));
+        }
+        float a, b;
+        f2_split(ax2, a, b);
+        ax0 = (Acc)a;
+        ax1 = (Acc)b;
+        f2_split(ay2, a, b);
+        ay0 = (Acc)a;
+        ay1 = (Acc)b;
+        f2_split(az2, a, b);
+        az0 = (Acc)a;
+        az1 = (Acc)b;
+    }
+    if (jl == 0) {
+        if (ia0 < mh) {
+            sm.hf[0][ia0] += ax0;
+            sm.hf[1][ia0] += ay0;
+            sm.hf[2][ia0] += az0;
+        }
+        if (ia1 < mh) {
+            sm.hf[0][ia1] += ax1;
+            sm.hf[1][ia1] += ay1;
+            sm.hf[2][ia1] += az1;
+        }
+    }
+}
+
 template <int MODE, bool ENERGY>
-__global__ void __launch_bounds__(kCT, MODE == MD_ACCUM_FIXED64 ? 5 : 7)
+__global__ void __launch_bounds__(kCT, MODE == MD_ACCUM_FIXED64 ? 6 : 7)
 k_cluster(CluArgs a)
 {
     using Acc = typename AccT<MODE>::T;
-    __shared__ __align__(16) float4 s_hp[kCTile];  // home tile (x, y, z shifted, q)
-    __shared__ __align__(16) float4 s_np[kCTile];  // neighbour tile
-    __shared__ int s_ht[kCTile], s_nt[kCTile];
-    __shared__ float s_ib[kCTile / kCI][6];  // i-cluster boxes: lo xyz, hi xyz
-    __shared__ float s_jb[kCTile / kCJ][6];  // j-cluster boxes
-    __shared__ Acc s_hf[3][kCTile];          // forces on home atoms (whole cell pair)
-    __shared__ Acc s_nf[kCW][3][kCTile];     // per-warp reactions on neighbour atoms (tile)
+    __shared__ __align__(16) CluSmem<MODE> sm;
     extern __shared__ __align__(16) unsigned char s_dyn[];
-    float2 *s_ab = reinterpret_cast<float2 *>(s_dyn);  // LJ table [ntypes * ntypes]
+    float2 *s_ab = reinterpret_cast<float2 *>(s_dyn);  // LJ table [ntypes * ntypes]: (A, -B)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int il = lane & (kCI - 1), jl = lane / kCI;
     float e_lj = 0.f, e_c = 0.f, vir = 0.f;
-    unsigned long long cnt = 0;
+    unsigned cnt = 0;
     Partial *mine = a.partials + (size_t)blockIdx.y * gridDim.x;
 
     PairGeom g;
@@ -160,15 +418,28 @@ k_cluster(CluArgs a)
         block_partial<kCT>(0.0, 0.0, 0.0, 0ull, mine);
         return;
     }
-    const int T = a.ntypes;
-    for (int t = threadIdx.x; t < T * T; t += kCT) s_ab[t] = a.AB[t];
-    const float kc = a.kc, rc2 = a.rc2, rc2m = a.rc2m;
+    CluConst k;
+    k.T = a.ntypes;
+    k.kc = a.kc;
+    k.rc2 = a.rc2;
+    k.rc2m = a.rc2m;
+    k.status = a.status;
+    bool shift = false;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        k.lo[d] = g.lo[d];
+        shift |= g.lo[d] != 0.0f;
+    }
+    for (int t = threadIdx.x; t < k.T * k.T; t += kCT) {
+        const float2 ab = a.AB[t];
+        s_ab[t] = make_float2(ab.x, -ab.y);
+    }
 
     for (int h0 = 0; h0 < nh; h0 += kCTile) {
         const int mh = min(kCTile, nh - h0);
-        const int nic = (mh + kCI - 1) / kCI;
+        const int nic = (mh + kCS - 1) / kCS;
         __syncthreads();
-        for (int t = threadIdx.x; t < nic * kCI; t += kCT) {
+        for (int t = threadIdx.x; t < nic * kCS; t += kCT) {
             float4 p;
             int ty = 0;
             if (t < mh) {
@@ -176,146 +447,66 @@ k_cluster(CluArgs a)
                 p.x -= g.hs[0];
                 p.y -= g.hs[1];
                 p.z -= g.hs[2];
-                ty = clamp_type(a.ty[h_begin + h0 + t], T, a.status);
+                ty = clamp_type(a.ty[h_begin + h0 + t], k.T, a.status);
             } else {
                 p = make_float4(kFar, kFar, kFar, 0.f);
             }
-            s_hp[t] = p;
-            s_ht[t] = ty;
-            s_hf[0][t] = s_hf[1][t] = s_hf[2][t] = Acc(0);
+            sm.hp[t] = p;
+            sm.ht[t] = ty;
+            sm.hf[0][t] = sm.hf[1][t] = sm.hf[2][t] = Acc(0);
         }
         __syncthreads();
-        cluster_boxes<kCI>(s_hp, mh, s_ib);
+        cluster_boxes(sm.hp, mh, sm.ib);
         for (int n0 = g.self ? h0 : 0; n0 < nn; n0 += kCTile) {
             const int mn = min(kCTile, nn - n0);
-            const int njc = (mn + kCJ - 1) / kCJ;
+            const int njc = (mn + kCS - 1) / kCS;
             const bool diag = g.self && n0 == h0;
             __syncthreads();
-            for (int t = threadIdx.x; t < njc * kCJ; t += kCT) {
+            for (int t = threadIdx.x; t < njc * kCS; t += kCT) {
                 float4 p;
                 int ty = 0;
                 if (t >= mn) {
                     p = make_float4(-kFar, -kFar, -kFar, 0.f);
                 } else if (diag) {
-                    p = s_hp[t];  // the home tile holds the same atoms
-                    ty = s_ht[t];
+                    p = sm.hp[t];  // the home tile holds the same atoms
+                    ty = sm.ht[t];
                 } else {
                     p = a.pq[n_begin + n0 + t];
                     p.x -= g.ns[0];
                     p.y -= g.ns[1];
                     p.z -= g.ns[2];
-                    ty = clamp_type(a.ty[n_begin + n0 + t], T, a.status);
+                    ty = clamp_type(a.ty[n_begin + n0 + t], k.T, a.status);
                 }
-                s_np[t] = p;
-                s_nt[t] = ty;
+                sm.np[t] = p;
+                sm.nt[t] = ty;
 #pragma unroll
-                for (int w = 0; w < kCW; ++w) s_nf[w][0][t] = s_nf[w][1][t] = s_nf[w][2][t] = Acc(0);
+                for (int w = 0; w < CluSmem<MODE>::NW; ++w) sm.nf[w][0][t] = sm.nf[w][1][t] = sm.nf[w][2][t] = Acc(0);
             }
             __syncthreads();
-            cluster_boxes<kCJ>(s_np, mn, s_jb);
+            cluster_boxes(sm.np, mn, sm.jb);
             __syncthreads();
-
-            Acc(*nf)[kCTile] = s_nf[warp];
             for (int ic = warp; ic < nic; ic += kCW) {
-                const int ia = ic * kCI + il;
-                const float4 pi = s_hp[ia];
-                const int tiT = s_ht[ia] * T;
-                float ib[6];
-#pragma unroll
-                for (int d = 0; d < 6; ++d) ib[d] = s_ib[ic][d];
-                Acc ax = Acc(0), ay = Acc(0), az = Acc(0);
-                // on the diagonal tile only j-clusters that hold some atom after ia
-                const int jc0 = diag ? (ic * kCI) / kCJ : 0;
-                for (int jb = jc0; jb < njc; jb += 32) {
-                    const int jt = jb + lane;
-                    bool in = false;
-                    if (jt < njc) {
-                        const float *q = s_jb[jt];
-                        const float gx = fmaxf(0.f, fmaxf(ib[0] - q[3], q[0] - ib[3]));
-                        const float gy = fmaxf(0.f, fmaxf(ib[1] - q[4], q[1] - ib[4]));
-                        const float gz = fmaxf(0.f, fmaxf(ib[2] - q[5], q[2] - ib[5]));
-                        in = gx * gx + gy * gy + gz * gz < rc2m;
-                    }
-                    unsigned todo = __ballot_sync(0xffffffffu, in);
-                    while (todo) {
-                        const int jc = jb + __ffs(todo) - 1;
-                        todo &= todo - 1;
-                        const int ja = jc * kCJ + jl;
-                        const float4 pj = s_np[ja];
-                        const float dx = (pi.x - pj.x) + g.lo[0];
-                        const float dy = (pi.y - pj.y) + g.lo[1];
-                        const float dz = (pi.z - pj.z) + g.lo[2];
-                        const float r2 = pair_r2(dx, dy, dz);
-                        const bool ok = r2 < rc2 && ja < mn && (!diag || ia < ja);
-                        const float2 ab = s_ab[tiT + s_nt[ja]];
-                        const float kqq = __fmul_rn(kc, __fmul_rn(pi.w, pj.w));
-                        float ir, ir2, ir6;
-                        float f = pair_f(r2, ab.x, ab.y, kqq, ir, ir2, ir6);
-                        f = ok ? f : 0.0f;
-                        const float fx = __fmul_rn(f, dx), fy = __fmul_rn(f, dy), fz = __fmul_rn(f, dz);
-                        Acc vx, vy, vz;
-                        if (MODE == MD_ACCUM_FIXED64) {
-                            vx = (Acc)(ok ? to_fixed(fx, a.status) : 0);
-                            vy = (Acc)(ok ? to_fixed(fy, a.status) : 0);
-                            vz = (Acc)(ok ? to_fixed(fz, a.status) : 0);
-                        } else {
-                            vx = (Acc)fx;
-                            vy = (Acc)fy;
-                            vz = (Acc)fz;
-                        }
-                        ax += vx;
-                        ay += vy;
-                        az += vz;
-                        // reaction on ja: sum over the kCI lanes that share it
-#pragma unroll
-                        for (int o = 1; o < kCI; o <<= 1) {
-                            vx += __shfl_xor_sync(0xffffffffu, vx, o);
-                            vy += __shfl_xor_sync(0xffffffffu, vy, o);
-                            vz += __shfl_xor_sync(0xffffffffu, vz, o);
-                        }
-                        if (il == 0) {
-                            nf[0][ja] -= vx;
-                            nf[1][ja] -= vy;
-                            nf[2][ja] -= vz;
-                        }
-                        if (ok) {
-                            cnt += 1;
-                            if (ENERGY) {
-                                e_lj += pair_u_lj(ab.x, ab.y, ir6);
-                                e_c += kqq * ir;
-                                vir += f * r2;
-                            }
-                        }
-                    }
-                }
-                // i-forces: sum over the kCJ lanes that share ia; the i-cluster belongs
-                // to this warp alone
-#pragma unroll
-                for (int o = kCI; o < 32; o <<= 1) {
-                    ax += __shfl_xor_sync(0xffffffffu, ax, o);
-                    ay += __shfl_xor_sync(0xffffffffu, ay, o);
-                    az += __shfl_xor_sync(0xffffffffu, az, o);
-                }
-                if (jl == 0 && ia < mh) {
-                    s_hf[0][ia] += ax;
-                    s_hf[1][ia] += ay;
-                    s_hf[2][ia] += az;
-                }
+                if (diag)
+                    cluster_row<MODE, ENERGY, true, false>(sm, s_ab, k, ic, njc, mh, warp, lane, e_lj, e_c, vir, cnt);
+                else if (shift)
+                    cluster_row<MODE, ENERGY, false, true>(sm, s_ab, k, ic, njc, mh, warp, lane, e_lj, e_c, vir, cnt);
+                else
+                    cluster_row<MODE, ENERGY, false, false>(sm, s_ab, k, ic, njc, mh, warp, lane, e_lj, e_c, vir, cnt);
             }
             __syncthreads();
             for (int t = threadIdx.x; t < mn; t += kCT) {
-                Acc sx = s_nf[0][0][t], sy = s_nf[0][1][t], sz = s_nf[0][2][t];
+                Acc sx = sm.nf[0][0][t], sy = sm.nf[0][1][t], sz = sm.nf[0][2][t];
 #pragma unroll
-                for (int w = 1; w < kCW; ++w) {
-                    sx += s_nf[w][0][t];
-                    sy += s_nf[w][1][t];
-                    sz += s_nf[w][2][t];
+                for (int w = 1; w < CluSmem<MODE>::NW; ++w) {
+                    sx += sm.nf[w][0][t];
+                    sy += sm.nf[w][1][t];
+                    sz += sm.nf[w][2][t];
                 }
                 if (diag) {
                     // the neighbour tile is the home tile: reactions join the home sums
-                    s_hf[0][t] += sx;
-                    s_hf[1][t] += sy;
-                    s_hf[2][t] += sz;
+                    sm.hf[0][t] += sx;
+                    sm.hf[1][t] += sy;
+                    sm.hf[2][t] += sz;
                 } else {
                     const int s = n_begin + n0 + t;
                     if (MODE == MD_ACCUM_FIXED64) {
@@ -334,16 +525,16 @@ k_cluster(CluArgs a)
             const int s = h_begin + h0 + t;
             if (MODE == MD_ACCUM_FIXED64) {
                 unsigned long long *acc = static_cast<unsigned long long *>(a.accum);
-                atomicAdd(&acc[s], (unsigned long long)s_hf[0][t]);
-                atomicAdd(&acc[(size_t)a.n + s], (unsigned long long)s_hf[1][t]);
-                atomicAdd(&acc[2 * (size_t)a.n + s], (unsigned long long)s_hf[2][t]);
+                atomicAdd(&acc[s], (unsigned long long)sm.hf[0][t]);
+                atomicAdd(&acc[(size_t)a.n + s], (unsigned long long)sm.hf[1][t]);
+                atomicAdd(&acc[2 * (size_t)a.n + s], (unsigned long long)sm.hf[2][t]);
             } else {
-                red_add_v4(static_cast<float4 *>(a.accum) + s, (float)s_hf[0][t], (float)s_hf[1][t],
-                           (float)s_hf[2][t]);
+                red_add_v4(static_cast<float4 *>(a.accum) + s, (float)sm.hf[0][t], (float)sm.hf[1][t],
+                           (float)sm.hf[2][t]);
             }
         }
     }
-    block_partial<kCT>((double)e_lj, (double)e_c, (double)vir, cnt, mine);
+    block_partial<kCT>((double)e_lj, (double)e_c, (double)vir, (unsigned long long)cnt, mine);
 }
 
 // Cluster-order accumulators -> forces_out in input order.
