@@ -249,16 +249,20 @@ int md_batch_step(int32_t nsys, const md_system_desc *systems, double *pos, doub
 /*
  * Kernel shapes of the batched force launches.  A shape is a performance choice only:
  * every shape finds the same pairs, and in MD_ACCUM_FIXED64 gives the same bits.
- *   0  default: 4 warps per block, 256 (F32) or 128 (FIXED64) buffered pairs per warp
- *   1  2 warps per block, 256 buffered pairs per warp
- *   2  8 warps per block, 256 buffered pairs per warp
- *   3  4 warps per block, 128 buffered pairs per warp
- * The buffer holds the filter's survivors of one 32x32 block of candidate pairs (the
- * paper's queue between distance and force stages, Section IV); a block that keeps more
- * is processed in several passes.  More warps per block share the block's staged cells
- * among more candidate blocks; fewer give more blocks per SM for small cells.
+ *   0  default: the cluster-pair kernel (MD_ALGO_CLUSTER) for systems with >= 3 cells
+ *      on every axis; shape 1 for systems with an axis of 2 cells
+ *   1  half-shell kernel, 4 warps per block, 256 (F32) or 128 (FIXED64) buffered pairs
+ *      per warp
+ *   2  half-shell kernel, 2 warps per block, 256 buffered pairs per warp
+ *   3  half-shell kernel, 8 warps per block, 256 buffered pairs per warp
+ *   4  half-shell kernel, 4 warps per block, 128 buffered pairs per warp
+ * The half-shell buffer holds the filter's survivors of one 32x32 block of candidate
+ * pairs (the paper's queue between distance and force stages, Section IV); a block that
+ * keeps more is processed in several passes.  More warps per block share the block's
+ * staged cells among more candidate blocks; fewer give more blocks per SM for small
+ * cells.
  */
-#define MD_BATCH_SHAPES 4
+#define MD_BATCH_SHAPES 5
 typedef struct md_batch_tuning {
     int32_t shape_regular; /* launch over the systems with >= 3 cells on every axis */
     int32_t shape_small;   /* launch over the systems with an axis of 2 cells */

@@ -46,15 +46,19 @@ constexpr int kOrderThreads = 256;
 
 static_assert(kCTile % kCS == 0 && kCTile / kCS <= 32, "a tile's clusters fit one ballot");
 // Per cell: sort its atoms by (column, z along the column) and write the reordered
-// copies.  corder[k] is the sorted-order slot of cluster-order slot k.
+// copies.  corder[k] is the sorted-order slot of cluster-order slot k.  BATCHED: cells
+// are numbered over the batch and each takes its system's box.
+template <bool BATCHED>
 __global__ void __launch_bounds__(kOrderThreads)
 k_cluster_order(const int32_t *__restrict__ cell_start, const float4 *__restrict__ pq,
-                const int32_t *__restrict__ ty, BoxF box, float4 *__restrict__ cpq,
-                int32_t *__restrict__ cty, int32_t *__restrict__ corder)
+                const int32_t *__restrict__ ty, BoxF box_in, BatchArgs bt,
+                float4 *__restrict__ cpq, int32_t *__restrict__ cty, int32_t *__restrict__ corder)
 {
     __shared__ unsigned long long s_key[kSortMax];
-    const int c = blockIdx.x;
-    const int b = cell_start[c], m = cell_start[c + 1] - b;
+    const int cg = blockIdx.x;
+    const BoxF &box = BATCHED ? bt.sys[bt.cell_sys[cg]].box : box_in;
+    const int c = BATCHED ? cg - bt.sys[bt.cell_sys[cg]].cell_offset : cg;
+    const int b = cell_start[cg], m = cell_start[cg + 1] - b;
     if (m <= 0) return;
     if (m > kSortMax) {
         for (int t = threadIdx.x; t < m; t += kOrderThreads) {
@@ -393,9 +397,9 @@ __device__ __forceinline__ void cluster_row(CluSmem<MODE> &sm, const float2 *s_a
     }
 }
 
-template <int MODE, bool ENERGY>
+template <int MODE, bool ENERGY, bool BATCHED>
 __global__ void __launch_bounds__(kCT, MODE == MD_ACCUM_FIXED64 ? 6 : 7)
-k_cluster(CluArgs a)
+k_cluster(CluArgs a, BatchArgs bt, unsigned long long *sys_pair_count)
 {
     using Acc = typename AccT<MODE>::T;
     __shared__ __align__(16) CluSmem<MODE> sm;
@@ -407,8 +411,33 @@ k_cluster(CluArgs a)
     unsigned cnt = 0;
     Partial *mine = a.partials + (size_t)blockIdx.y * gridDim.x;
 
+    // the system this CTA works on: the only one, or the one its cell belongs to
     PairGeom g;
-    if (!cell_pair(a.box, blockIdx.x, blockIdx.y, g)) {
+    CluConst k;
+    const float2 *AB;
+    bool valid;
+    int sid = 0;
+    if (BATCHED) {
+        const int cell = bt.cell_list[blockIdx.x];  // systems with >= 3 cells per axis
+        sid = bt.cell_sys[cell];
+        const SysDesc &d = bt.sys[sid];
+        valid = cell_pair(d.box, cell - d.cell_offset, blockIdx.y, g);
+        g.home += d.cell_offset;
+        g.nbr += d.cell_offset;
+        k.T = d.ntypes;
+        AB = d.AB;
+        k.kc = d.kc;
+        k.rc2 = d.rc2;
+        k.rc2m = d.rc2m;
+    } else {
+        valid = cell_pair(a.box, blockIdx.x, blockIdx.y, g);
+        k.T = a.ntypes;
+        AB = a.AB;
+        k.kc = a.kc;
+        k.rc2 = a.rc2;
+        k.rc2m = a.rc2m;
+    }
+    if (!valid) {
         block_partial<kCT>(0.0, 0.0, 0.0, 0ull, mine);
         return;
     }
@@ -418,11 +447,6 @@ k_cluster(CluArgs a)
         block_partial<kCT>(0.0, 0.0, 0.0, 0ull, mine);
         return;
     }
-    CluConst k;
-    k.T = a.ntypes;
-    k.kc = a.kc;
-    k.rc2 = a.rc2;
-    k.rc2m = a.rc2m;
     k.status = a.status;
     bool shift = false;
 #pragma unroll
@@ -431,7 +455,7 @@ k_cluster(CluArgs a)
         shift |= g.lo[d] != 0.0f;
     }
     for (int t = threadIdx.x; t < k.T * k.T; t += kCT) {
-        const float2 ab = a.AB[t];
+        const float2 ab = AB[t];
         s_ab[t] = make_float2(ab.x, -ab.y);
     }
 
@@ -535,6 +559,8 @@ k_cluster(CluArgs a)
         }
     }
     block_partial<kCT>((double)e_lj, (double)e_c, (double)vir, (unsigned long long)cnt, mine);
+    if (BATCHED && sys_pair_count && threadIdx.x == 0 && mine[blockIdx.x].count)
+        atomicAdd(&sys_pair_count[sid], mine[blockIdx.x].count);
 }
 
 // Cluster-order accumulators -> forces_out in input order.
@@ -563,15 +589,16 @@ k_finalize_clu(const void *__restrict__ accum, const int32_t *__restrict__ corde
     }
 }
 
-template <int MODE, bool ENERGY>
-void launch_cluster_t(const CluArgs &c, dim3 grid, cudaStream_t stream)
+template <int MODE, bool ENERGY, bool BATCHED = false>
+void launch_cluster_t(const CluArgs &c, dim3 grid, cudaStream_t stream, const BatchArgs &b = BatchArgs{},
+                      unsigned long long *sys_pair_count = nullptr)
 {
     const size_t dyn = sizeof(float2) * (size_t)c.ntypes * (size_t)c.ntypes;
     static const cudaError_t attr = cudaFuncSetAttribute(
-        k_cluster<MODE, ENERGY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        k_cluster<MODE, ENERGY, BATCHED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
         (int)(sizeof(float2) * kMaxTypes * kMaxTypes));
     (void)attr;
-    k_cluster<MODE, ENERGY><<<grid, kCT, dyn, stream>>>(c);
+    k_cluster<MODE, ENERGY, BATCHED><<<grid, kCT, dyn, stream>>>(c, b, sys_pair_count);
 }
 
 }  // namespace
@@ -591,8 +618,8 @@ cudaError_t launch_cluster(const ForceArgs &a, const WsLayout &ws, char *wsp, Pa
     int32_t *corder = reinterpret_cast<int32_t *>(wsp + ws.clu_order);
     cudaError_t e = cudaMemsetAsync(accum, 0, acc_bytes, stream);
     if (e != cudaSuccess) return e;
-    k_cluster_order<<<a.box.ncell, kOrderThreads, 0, stream>>>(a.cell_start, a.pos_q_sorted,
-                                                               a.type_sorted, a.box, cpq, cty, corder);
+    k_cluster_order<false><<<a.box.ncell, kOrderThreads, 0, stream>>>(
+        a.cell_start, a.pos_q_sorted, a.type_sorted, a.box, BatchArgs{}, cpq, cty, corder);
     CluArgs c;
     c.cell_start = a.cell_start;
     c.pq = cpq;
@@ -619,6 +646,59 @@ cudaError_t launch_cluster(const ForceArgs &a, const WsLayout &ws, char *wsp, Pa
         k_finalize_clu<MD_ACCUM_F32><<<g, 256, 0, stream>>>(accum, corder, a.perm, a.n, a.forces_out, a.status);
     }
     *nblocks_out = a.box.ncell * 14;
+    return cudaGetLastError();
+}
+
+// Batched: cluster order of every cell of the batch (all systems), so that both force
+// launches (cluster kernel for the regular systems, half-shell kernel for the 2-cell
+// boxes) read cluster-ordered tiles and accumulate in cluster order.
+cudaError_t launch_cluster_order_batched(const ForceArgs &a, const BatchArgs &b, const WsLayout &ws,
+                                         char *wsp, cudaStream_t stream)
+{
+    if (b.ncell <= 0) return cudaSuccess;
+    k_cluster_order<true><<<b.ncell, kOrderThreads, 0, stream>>>(
+        a.cell_start, a.pos_q_sorted, a.type_sorted, BoxF{}, b,
+        reinterpret_cast<float4 *>(wsp + ws.clu_pos_q), reinterpret_cast<int32_t *>(wsp + ws.clu_type),
+        reinterpret_cast<int32_t *>(wsp + ws.clu_order));
+    return cudaGetLastError();
+}
+
+// Batched cluster kernel over the regular systems' cells (b.cell_list[0 .. ncell_reg)).
+cudaError_t launch_cluster_batched(int mode, const BatchArgs &b, const int32_t *cell_start,
+                                   void *accum, Partial *partials, uint32_t *status,
+                                   unsigned long long *sys_pair_count, const WsLayout &ws,
+                                   char *wsp, cudaStream_t stream)
+{
+    if (b.ncell_reg <= 0) return cudaSuccess;
+    CluArgs c = {};
+    c.cell_start = cell_start;
+    c.pq = reinterpret_cast<const float4 *>(wsp + ws.clu_pos_q);
+    c.ty = reinterpret_cast<const int32_t *>(wsp + ws.clu_type);
+    c.ntypes = b.max_ntypes;  // sizes the shared LJ table
+    c.accum = accum;
+    c.n = b.n;
+    c.partials = partials;
+    c.status = status;
+    dim3 grid(b.ncell_reg, 14);
+    if (mode == MD_ACCUM_FIXED64)
+        launch_cluster_t<MD_ACCUM_FIXED64, false, true>(c, grid, stream, b, sys_pair_count);
+    else
+        launch_cluster_t<MD_ACCUM_F32, false, true>(c, grid, stream, b, sys_pair_count);
+    return cudaGetLastError();
+}
+
+// Cluster-order accumulators -> forces in input order (batched or not).
+cudaError_t launch_finalize_cluster(int mode, const void *accum, const WsLayout &ws, char *wsp,
+                                    const int32_t *perm, int n, void *forces_out, uint32_t *status,
+                                    cudaStream_t stream)
+{
+    if (n <= 0) return cudaSuccess;
+    const int32_t *corder = reinterpret_cast<const int32_t *>(wsp + ws.clu_order);
+    const int g = (n + 255) / 256;
+    if (mode == MD_ACCUM_FIXED64)
+        k_finalize_clu<MD_ACCUM_FIXED64><<<g, 256, 0, stream>>>(accum, corder, perm, n, forces_out, status);
+    else
+        k_finalize_clu<MD_ACCUM_F32><<<g, 256, 0, stream>>>(accum, corder, perm, n, forces_out, status);
     return cudaGetLastError();
 }
 

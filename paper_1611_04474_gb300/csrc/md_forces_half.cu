@@ -530,18 +530,19 @@ void launch_half_t(const HalfArgs &h, dim3 grid, cudaStream_t stream, const Batc
     k_half_shell<MODE, ENERGY, MI, BATCHED, W, CAP><<<grid, W * 32, dyn, stream>>>(h, b, sys_pair_count);
 }
 
-// The batched launches' kernel shapes (md_batch_tuning): {warps per CTA, survivors
-// buffered per warp} = 0 {4, default}, 1 {2, 256}, 2 {8, 256}, 3 {4, 128}.
-static_assert(MD_BATCH_SHAPES == 4, "one case per shape");
+// The half-shell shapes of the batched launches (md_batch_tuning): {warps per CTA,
+// survivors buffered per warp} = 1 {4, default}, 2 {2, 256}, 3 {8, 256}, 4 {4, 128}.
+// Shape 0 is the cluster kernel for regular cells and shape 1 for 2-cell boxes.
+static_assert(MD_BATCH_SHAPES == 5, "one case per shape");
 
 template <int MODE, bool MI>
 void launch_batched_shape(int shape, const HalfArgs &h, dim3 grid, cudaStream_t stream,
                           const BatchArgs &b, unsigned long long *cnt)
 {
     switch (shape) {
-    case 1: launch_half_t<MODE, false, MI, true, 2, 256>(h, grid, stream, b, cnt); break;
-    case 2: launch_half_t<MODE, false, MI, true, 8, 256>(h, grid, stream, b, cnt); break;
-    case 3: launch_half_t<MODE, false, MI, true, 4, 128>(h, grid, stream, b, cnt); break;
+    case 2: launch_half_t<MODE, false, MI, true, 2, 256>(h, grid, stream, b, cnt); break;
+    case 3: launch_half_t<MODE, false, MI, true, 8, 256>(h, grid, stream, b, cnt); break;
+    case 4: launch_half_t<MODE, false, MI, true, 4, 128>(h, grid, stream, b, cnt); break;
     default: launch_half_t<MODE, false, MI, true, 4, KCap<MODE>::value>(h, grid, stream, b, cnt); break;
     }
 }
@@ -574,10 +575,13 @@ cudaError_t launch_forces_batched(const ForceArgs &a, const BatchArgs &b,
     void *accum = wsp + ws.accum;
     cudaError_t e = cudaMemsetAsync(accum, 0, acc_bytes, stream);
     if (e != cudaSuccess) return e;
+    // every cell in cluster order; both launches read those copies and accumulate in
+    // cluster order
+    if ((e = launch_cluster_order_batched(a, b, ws, wsp, stream)) != cudaSuccess) return e;
     HalfArgs h = {};
     h.cell_start = a.cell_start;
-    h.pq = a.pos_q_sorted;
-    h.ty = a.type_sorted;
+    h.pq = reinterpret_cast<const float4 *>(wsp + ws.clu_pos_q);
+    h.ty = reinterpret_cast<const int32_t *>(wsp + ws.clu_type);
     h.accum = accum;
     h.n = b.n;
     h.status = a.status;
@@ -587,8 +591,12 @@ cudaError_t launch_forces_batched(const ForceArgs &a, const BatchArgs &b,
     if (b.ncell_reg > 0) {
         h.partials = partials;
         dim3 grid(b.ncell_reg, 14);
-        if (a.mode == MD_ACCUM_FIXED64) launch_batched_shape<MD_ACCUM_FIXED64, false>(shape_reg, h, grid, stream, b, sys_pair_count);
+        if (shape_reg == 0)
+            e = launch_cluster_batched(a.mode, b, a.cell_start, accum, partials, a.status, sys_pair_count,
+                                       ws, wsp, stream);
+        else if (a.mode == MD_ACCUM_FIXED64) launch_batched_shape<MD_ACCUM_FIXED64, false>(shape_reg, h, grid, stream, b, sys_pair_count);
         else launch_batched_shape<MD_ACCUM_F32, false>(shape_reg, h, grid, stream, b, sys_pair_count);
+        if (e != cudaSuccess) return e;
     }
     if (b.ncell_mi > 0) {
         h.partials = partials + (size_t)14 * b.ncell_reg;
@@ -596,13 +604,9 @@ cudaError_t launch_forces_batched(const ForceArgs &a, const BatchArgs &b,
         if (a.mode == MD_ACCUM_FIXED64) launch_batched_shape<MD_ACCUM_FIXED64, true>(shape_mi, h, grid, stream, b, sys_pair_count);
         else launch_batched_shape<MD_ACCUM_F32, true>(shape_mi, h, grid, stream, b, sys_pair_count);
     }
-    const int g = (b.n + 255) / 256;
-    if (g > 0) {
-        if (a.mode == MD_ACCUM_FIXED64)
-            k_finalize<MD_ACCUM_FIXED64><<<g, 256, 0, stream>>>(accum, a.perm, b.n, a.forces_out, a.status);
-        else
-            k_finalize<MD_ACCUM_F32><<<g, 256, 0, stream>>>(accum, a.perm, b.n, a.forces_out, a.status);
-    }
+    if ((e = launch_finalize_cluster(a.mode, accum, ws, wsp, a.perm, b.n, a.forces_out, a.status, stream)) !=
+        cudaSuccess)
+        return e;
     return cudaGetLastError();
 }
 

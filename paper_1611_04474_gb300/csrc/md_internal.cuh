@@ -257,6 +257,9 @@ void cutoff_thresholds(const BoxF &box, double rc, bool mi, float *rc2, float *r
 cudaError_t launch_half_shell(const ForceArgs &a, const WsLayout &ws, char *wsp, Partial *partials,
                               int *nblocks_out, cudaStream_t stream);
 bool cluster_kernel_applies(const BoxF &box);
+cudaError_t launch_finalize_cluster(int mode, const void *accum, const WsLayout &ws, char *wsp,
+                                    const int32_t *perm, int n, void *forces_out, uint32_t *status,
+                                    cudaStream_t stream);
 cudaError_t launch_cluster(const ForceArgs &a, const WsLayout &ws, char *wsp, Partial *partials,
                            int *nblocks_out, cudaStream_t stream);
 
@@ -269,6 +272,12 @@ struct BatchArgs {
     int nsys, n, ncell, ncell_mi, ncell_reg;
     int max_ntypes;  // largest LJ table of the batch: sizes the kernels' shared copy
 };
+cudaError_t launch_cluster_order_batched(const ForceArgs &a, const BatchArgs &b, const WsLayout &ws,
+                                         char *wsp, cudaStream_t stream);
+cudaError_t launch_cluster_batched(int mode, const BatchArgs &b, const int32_t *cell_start,
+                                   void *accum, Partial *partials, uint32_t *status,
+                                   unsigned long long *sys_pair_count, const WsLayout &ws,
+                                   char *wsp, cudaStream_t stream);
 cudaError_t launch_build_cells_batched(const float4 *pos_q, const int32_t *type, const BatchArgs &b,
                                        int32_t *cell_start, int32_t *perm, float4 *pos_q_sorted,
                                        int32_t *type_sorted, const WsLayout &ws, char *wsp,
