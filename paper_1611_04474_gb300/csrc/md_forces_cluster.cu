@@ -45,6 +45,12 @@ constexpr int kSortMax = 1024;  // cells with more atoms keep their sorted order
 constexpr int kOrderThreads = 256;
 
 static_assert(kCTile % kCS == 0 && kCTile / kCS <= 32, "a tile's clusters fit one ballot");
+
+// What a launch accumulates besides the forces (the partials are written only when
+// asked for).
+constexpr int kStatsNone = 0;    // forces only
+constexpr int kStatsCount = 1;   // + within-cutoff pair count
+constexpr int kStatsEnergy = 2;  // + count, energies and virial
 // Per cell: sort its atoms by (column, z along the column) and write the reordered
 // copies.  corder[k] is the sorted-order slot of cluster-order slot k.  BATCHED: cells
 // are numbered over the batch and each takes its system's box.
@@ -139,7 +145,7 @@ struct CluArgs {
 };
 
 // Bounding boxes of the clusters of a staged tile (padding excluded).
-__device__ __forceinline__ void cluster_boxes(const float4 *p, int m, float (*box)[6])
+__device__ __forceinline__ void cluster_boxes(const float4 *p, int m, float (*box)[kCTile / kCS])
 {
     const int nclu = (m + kCS - 1) / kCS;
     for (int k = threadIdx.x; k < nclu; k += kCT) {
@@ -153,8 +159,8 @@ __device__ __forceinline__ void cluster_boxes(const float4 *p, int m, float (*bo
         }
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            box[k][d] = lo[d];
-            box[k][d + 3] = hi[d];
+            box[d][k] = lo[d];
+            box[d + 3][k] = hi[d];
         }
     }
 }
@@ -168,10 +174,11 @@ struct CluSmem {
     float4 hp[kCTile];  // home tile (x, y, z shifted, q)
     float4 np[kCTile];  // neighbour tile
     int ht[kCTile], nt[kCTile];
-    float ib[kCTile / kCS][6];  // home cluster boxes: lo xyz, hi xyz
-    float jb[kCTile / kCS][6];  // neighbour cluster boxes
+    float ib[6][kCTile / kCS];  // home cluster boxes: lo xyz, hi xyz (one row per bound)
+    float jb[6][kCTile / kCS];  // neighbour cluster boxes
     Acc hf[3][kCTile];          // forces on home atoms (whole cell pair)
     Acc nf[NW][3][kCTile];      // reactions on neighbour atoms (this tile)
+    int next;                   // next home cluster to hand out
 };
 
 struct CluConst {
@@ -184,7 +191,7 @@ struct CluConst {
 // Home cluster ic against every neighbour cluster of the staged tile in range.
 // DIAG: the neighbour tile is the home tile (pairs ia < ja only); SHIFT: the cell
 // pair has a remainder shift to add to the difference.
-template <int MODE, bool ENERGY, bool DIAG, bool SHIFT>
+template <int MODE, int STATS, bool DIAG, bool SHIFT>
 __device__ __forceinline__ void cluster_row(CluSmem<MODE> &sm, const float2 *s_ab,
                                             const CluConst &k, int ic, int njc, int mh, int warp,
                                             int lane, float &e_lj, float &e_c, float &vir,
@@ -197,12 +204,13 @@ __device__ __forceinline__ void cluster_row(CluSmem<MODE> &sm, const float2 *s_a
     const f2 xi = f2_make(p0.x, p1.x), yi = f2_make(p0.y, p1.y), zi = f2_make(p0.z, p1.z);
     const f2 qi = f2_make(p0.w, p1.w);
     const int t0 = sm.ht[ia0] * k.T, t1 = sm.ht[ia1] * k.T;
-    const f2 kc2 = f2_make(k.kc, k.kc), m05 = f2_make(-0.5f, -0.5f), c15 = f2_make(1.5f, 1.5f);
+    const f2 kcq = f2_mul(f2_make(k.kc, k.kc), qi);  // k q_i (F32 path)
+    const f2 m05 = f2_make(-0.5f, -0.5f), c15 = f2_make(1.5f, 1.5f);
     const f2 lox = f2_make(k.lo[0], k.lo[0]), loy = f2_make(k.lo[1], k.lo[1]),
              loz = f2_make(k.lo[2], k.lo[2]);
     float ib[6];
 #pragma unroll
-    for (int d = 0; d < 6; ++d) ib[d] = sm.ib[ic][d];
+    for (int d = 0; d < 6; ++d) ib[d] = sm.ib[d][ic];
     // home-atom sums: F32 packed (atom ia0 low, ia1 high); FIXED64 one integer each
     f2 ax2 = 0ull, ay2 = 0ull, az2 = 0ull;
     Acc ax0 = Acc(0), ay0 = Acc(0), az0 = Acc(0), ax1 = Acc(0), ay1 = Acc(0), az1 = Acc(0);
@@ -212,10 +220,9 @@ __device__ __forceinline__ void cluster_row(CluSmem<MODE> &sm, const float2 *s_a
         const int jt = jb + lane;
         bool in = false;
         if (jt < njc) {
-            const float *q = sm.jb[jt];
-            const float gx = fmaxf(0.f, fmaxf(ib[0] - q[3], q[0] - ib[3]));
-            const float gy = fmaxf(0.f, fmaxf(ib[1] - q[4], q[1] - ib[4]));
-            const float gz = fmaxf(0.f, fmaxf(ib[2] - q[5], q[2] - ib[5]));
+            const float gx = fmaxf(0.f, fmaxf(ib[0] - sm.jb[3][jt], sm.jb[0][jt] - ib[3]));
+            const float gy = fmaxf(0.f, fmaxf(ib[1] - sm.jb[4][jt], sm.jb[1][jt] - ib[4]));
+            const float gz = fmaxf(0.f, fmaxf(ib[2] - sm.jb[5][jt], sm.jb[2][jt] - ib[5]));
             in = gx * gx + gy * gy + gz * gz < k.rc2m;
         }
         unsigned todo = __ballot_sync(0xffffffffu, in);
@@ -260,8 +267,8 @@ __device__ __forceinline__ void cluster_row(CluSmem<MODE> &sm, const float2 *s_a
                 vx = g0[0] + g1[0];
                 vy = g0[1] + g1[1];
                 vz = g0[2] + g1[2];
-                cnt += (unsigned)ok0 + (unsigned)ok1;
-                if (ENERGY) {
+                if (STATS >= kStatsCount) cnt += (unsigned)ok0 + (unsigned)ok1;
+                if (STATS == kStatsEnergy) {
                     if (ok0) {
                         e_lj += pair_u_lj(ab0.x, -ab0.y, ir60);
                         e_c += kqq0 * ir0;
@@ -287,7 +294,7 @@ __device__ __forceinline__ void cluster_row(CluSmem<MODE> &sm, const float2 *s_a
                 const bool ok0 = r20 < k.rc2 && (!DIAG || ia0 < ja);
                 const bool ok1 = r21 < k.rc2 && (!DIAG || ia1 < ja);
                 const f2 A2 = f2_make(ab0.x, ab1.x), nB2 = f2_make(ab0.y, ab1.y);
-                const f2 kqq = f2_mul(kc2, f2_mul(qi, f2_dup(pj.w)));
+                const f2 kqq = f2_mul(kcq, f2_dup(pj.w));
                 // pair_f, element by element: rsqrt_nr, the powers, Eq. 1 + Eq. 2
                 float y0, y1;
                 asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(r20));
@@ -315,8 +322,8 @@ __device__ __forceinline__ void cluster_row(CluSmem<MODE> &sm, const float2 *s_a
                 vy = (Acc)(a0 + a1);
                 f2_split(fz, a0, a1);
                 vz = (Acc)(a0 + a1);
-                cnt += (unsigned)ok0 + (unsigned)ok1;
-                if (ENERGY) {
+                if (STATS >= kStatsCount) cnt += (unsigned)ok0 + (unsigned)ok1;
+                if (STATS == kStatsEnergy) {
                     float i6a, i6b, ira, irb, ka, kb;
                     f2_split(ir6, i6a, i6b);
                     f2_split(ir, ira, irb);
@@ -397,7 +404,7 @@ __device__ __forceinline__ void cluster_row(CluSmem<MODE> &sm, const float2 *s_a
     }
 }
 
-template <int MODE, bool ENERGY, bool BATCHED>
+template <int MODE, int STATS, bool BATCHED>
 __global__ void __launch_bounds__(kCT, MODE == MD_ACCUM_FIXED64 ? 6 : 7)
 k_cluster(CluArgs a, BatchArgs bt, unsigned long long *sys_pair_count)
 {
@@ -438,13 +445,13 @@ k_cluster(CluArgs a, BatchArgs bt, unsigned long long *sys_pair_count)
         k.rc2m = a.rc2m;
     }
     if (!valid) {
-        block_partial<kCT>(0.0, 0.0, 0.0, 0ull, mine);
+        if (STATS != kStatsNone) block_partial<kCT>(0.0, 0.0, 0.0, 0ull, mine);
         return;
     }
     const int h_begin = a.cell_start[g.home], nh = a.cell_start[g.home + 1] - h_begin;
     const int n_begin = a.cell_start[g.nbr], nn = a.cell_start[g.nbr + 1] - n_begin;
     if (nh == 0 || nn == 0) {
-        block_partial<kCT>(0.0, 0.0, 0.0, 0ull, mine);
+        if (STATS != kStatsNone) block_partial<kCT>(0.0, 0.0, 0.0, 0ull, mine);
         return;
     }
     k.status = a.status;
@@ -508,14 +515,19 @@ k_cluster(CluArgs a, BatchArgs bt, unsigned long long *sys_pair_count)
             }
             __syncthreads();
             cluster_boxes(sm.np, mn, sm.jb);
+            if (threadIdx.x == 0) sm.next = kCW;
             __syncthreads();
-            for (int ic = warp; ic < nic; ic += kCW) {
+            // home clusters handed out one at a time, so that warps finish together
+            for (int ic = warp; ic < nic;) {
                 if (diag)
-                    cluster_row<MODE, ENERGY, true, false>(sm, s_ab, k, ic, njc, mh, warp, lane, e_lj, e_c, vir, cnt);
+                    cluster_row<MODE, STATS, true, false>(sm, s_ab, k, ic, njc, mh, warp, lane, e_lj, e_c, vir, cnt);
                 else if (shift)
-                    cluster_row<MODE, ENERGY, false, true>(sm, s_ab, k, ic, njc, mh, warp, lane, e_lj, e_c, vir, cnt);
+                    cluster_row<MODE, STATS, false, true>(sm, s_ab, k, ic, njc, mh, warp, lane, e_lj, e_c, vir, cnt);
                 else
-                    cluster_row<MODE, ENERGY, false, false>(sm, s_ab, k, ic, njc, mh, warp, lane, e_lj, e_c, vir, cnt);
+                    cluster_row<MODE, STATS, false, false>(sm, s_ab, k, ic, njc, mh, warp, lane, e_lj, e_c, vir, cnt);
+                int nx = 0;
+                if (lane == 0) nx = atomicAdd(&sm.next, 1);
+                ic = __shfl_sync(0xffffffffu, nx, 0);
             }
             __syncthreads();
             for (int t = threadIdx.x; t < mn; t += kCT) {
@@ -558,9 +570,11 @@ k_cluster(CluArgs a, BatchArgs bt, unsigned long long *sys_pair_count)
             }
         }
     }
-    block_partial<kCT>((double)e_lj, (double)e_c, (double)vir, (unsigned long long)cnt, mine);
-    if (BATCHED && sys_pair_count && threadIdx.x == 0 && mine[blockIdx.x].count)
-        atomicAdd(&sys_pair_count[sid], mine[blockIdx.x].count);
+    if (STATS != kStatsNone) {
+        block_partial<kCT>((double)e_lj, (double)e_c, (double)vir, (unsigned long long)cnt, mine);
+        if (BATCHED && sys_pair_count && threadIdx.x == 0 && mine[blockIdx.x].count)
+            atomicAdd(&sys_pair_count[sid], mine[blockIdx.x].count);
+    }
 }
 
 // Cluster-order accumulators -> forces_out in input order.
@@ -589,16 +603,16 @@ k_finalize_clu(const void *__restrict__ accum, const int32_t *__restrict__ corde
     }
 }
 
-template <int MODE, bool ENERGY, bool BATCHED = false>
+template <int MODE, int STATS, bool BATCHED = false>
 void launch_cluster_t(const CluArgs &c, dim3 grid, cudaStream_t stream, const BatchArgs &b = BatchArgs{},
                       unsigned long long *sys_pair_count = nullptr)
 {
     const size_t dyn = sizeof(float2) * (size_t)c.ntypes * (size_t)c.ntypes;
     static const cudaError_t attr = cudaFuncSetAttribute(
-        k_cluster<MODE, ENERGY, BATCHED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        k_cluster<MODE, STATS, BATCHED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
         (int)(sizeof(float2) * kMaxTypes * kMaxTypes));
     (void)attr;
-    k_cluster<MODE, ENERGY, BATCHED><<<grid, kCT, dyn, stream>>>(c, b, sys_pair_count);
+    k_cluster<MODE, STATS, BATCHED><<<grid, kCT, dyn, stream>>>(c, b, sys_pair_count);
 }
 
 }  // namespace
@@ -634,15 +648,17 @@ cudaError_t launch_cluster(const ForceArgs &a, const WsLayout &ws, char *wsp, Pa
     c.partials = partials;
     c.status = a.status;
     dim3 grid(a.box.ncell, 14);
-    const bool en = a.energy_virial_out != nullptr;
+    const int stats = a.energy_virial_out ? kStatsEnergy : (a.pair_count_out ? kStatsCount : kStatsNone);
     const int g = (a.n + 255) / 256;
     if (a.mode == MD_ACCUM_FIXED64) {
-        if (en) launch_cluster_t<MD_ACCUM_FIXED64, true>(c, grid, stream);
-        else launch_cluster_t<MD_ACCUM_FIXED64, false>(c, grid, stream);
+        if (stats == kStatsEnergy) launch_cluster_t<MD_ACCUM_FIXED64, kStatsEnergy>(c, grid, stream);
+        else if (stats == kStatsCount) launch_cluster_t<MD_ACCUM_FIXED64, kStatsCount>(c, grid, stream);
+        else launch_cluster_t<MD_ACCUM_FIXED64, kStatsNone>(c, grid, stream);
         k_finalize_clu<MD_ACCUM_FIXED64><<<g, 256, 0, stream>>>(accum, corder, a.perm, a.n, a.forces_out, a.status);
     } else {
-        if (en) launch_cluster_t<MD_ACCUM_F32, true>(c, grid, stream);
-        else launch_cluster_t<MD_ACCUM_F32, false>(c, grid, stream);
+        if (stats == kStatsEnergy) launch_cluster_t<MD_ACCUM_F32, kStatsEnergy>(c, grid, stream);
+        else if (stats == kStatsCount) launch_cluster_t<MD_ACCUM_F32, kStatsCount>(c, grid, stream);
+        else launch_cluster_t<MD_ACCUM_F32, kStatsNone>(c, grid, stream);
         k_finalize_clu<MD_ACCUM_F32><<<g, 256, 0, stream>>>(accum, corder, a.perm, a.n, a.forces_out, a.status);
     }
     *nblocks_out = a.box.ncell * 14;
@@ -680,10 +696,13 @@ cudaError_t launch_cluster_batched(int mode, const BatchArgs &b, const int32_t *
     c.partials = partials;
     c.status = status;
     dim3 grid(b.ncell_reg, 14);
-    if (mode == MD_ACCUM_FIXED64)
-        launch_cluster_t<MD_ACCUM_FIXED64, false, true>(c, grid, stream, b, sys_pair_count);
-    else
-        launch_cluster_t<MD_ACCUM_F32, false, true>(c, grid, stream, b, sys_pair_count);
+    if (mode == MD_ACCUM_FIXED64) {
+        if (sys_pair_count) launch_cluster_t<MD_ACCUM_FIXED64, kStatsCount, true>(c, grid, stream, b, sys_pair_count);
+        else launch_cluster_t<MD_ACCUM_FIXED64, kStatsNone, true>(c, grid, stream, b, nullptr);
+    } else {
+        if (sys_pair_count) launch_cluster_t<MD_ACCUM_F32, kStatsCount, true>(c, grid, stream, b, sys_pair_count);
+        else launch_cluster_t<MD_ACCUM_F32, kStatsNone, true>(c, grid, stream, b, nullptr);
+    }
     return cudaGetLastError();
 }
 
