@@ -17,12 +17,13 @@
 //            candidates).
 //   force:   a warp evaluates the 8 x 8 pairs of one cluster pair: lane i + 4 j holds
 //            home atoms i and i + 4 and neighbour atom j and evaluates those two pairs,
-//            with the exact test r^2 < rc^2 per pair.  MD_ACCUM_F32 evaluates them
-//            with packed FP32x2 instructions (Blackwell's paired FP32 ALU);
-//            MD_ACCUM_FIXED64 with the library's scalar pair_r2 / pair_f on the same
-//            staged coordinates and shifts as the half-shell kernel, so its integers
-//            are the same bits as the other kernels' (the compiler may contract packed
-//            multiply-adds, which would move a pair force by an ulp).
+//            with packed FP32x2 instructions (Blackwell's paired FP32 ALU) and the
+//            exact test r^2 < rc^2 per pair.  The packed chain is pair_r2 / pair_f
+//            element by element on the same staged coordinates and shifts as the
+//            half-shell kernel, and every packed instruction rounds as its scalar
+//            counterpart, so MD_ACCUM_FIXED64 integers are the same bits as the other
+//            kernels'.  (pair_f ends in a fused multiply-add: a separate multiply
+//            feeding an add was fused by the compiler in the packed chain only.)
 //   reduce:  home-atom forces stay in registers for the whole home cluster; the
 //            reaction on each neighbour atom is summed over its two pairs, then over
 //            its 4 lanes by two shuffles, and added to a warp-private shared array
@@ -204,7 +205,8 @@ __device__ __forceinline__ void cluster_row(CluSmem<MODE> &sm, const float2 *s_a
     const f2 xi = f2_make(p0.x, p1.x), yi = f2_make(p0.y, p1.y), zi = f2_make(p0.z, p1.z);
     const f2 qi = f2_make(p0.w, p1.w);
     const int t0 = sm.ht[ia0] * k.T, t1 = sm.ht[ia1] * k.T;
-    const f2 kcq = f2_mul(f2_make(k.kc, k.kc), qi);  // k q_i (F32 path)
+    const f2 kc2 = f2_make(k.kc, k.kc);
+    const f2 kcq = f2_mul(kc2, qi);  // k q_i (F32 path)
     const f2 m05 = f2_make(-0.5f, -0.5f), c15 = f2_make(1.5f, 1.5f);
     const f2 lox = f2_make(k.lo[0], k.lo[0]), loy = f2_make(k.lo[1], k.lo[1]),
              loz = f2_make(k.lo[2], k.lo[2]);
@@ -233,85 +235,55 @@ __device__ __forceinline__ void cluster_row(CluSmem<MODE> &sm, const float2 *s_a
             const float4 pj = sm.np[ja];
             const int tj = sm.nt[ja];
             const float2 ab0 = s_ab[t0 + tj], ab1 = s_ab[t1 + tj];  // (A, -B)
+            // pair_r2 and pair_f element by element in packed FP32x2 instructions
+            // (each rounds as its scalar counterpart)
+            f2 dx = f2_sub(xi, f2_dup(pj.x)), dy = f2_sub(yi, f2_dup(pj.y)), dz = f2_sub(zi, f2_dup(pj.z));
+            if (SHIFT) {
+                dx = f2_add(dx, lox);
+                dy = f2_add(dy, loy);
+                dz = f2_add(dz, loz);
+            }
+            const f2 r2 = f2_fma(dz, dz, f2_fma(dy, dy, f2_mul(dx, dx)));
+            float r20, r21;
+            f2_split(r2, r20, r21);
+            // padding sits at +-1e18: such pairs fail the cutoff test
+            const bool ok0 = r20 < k.rc2 && (!DIAG || ia0 < ja);
+            const bool ok1 = r21 < k.rc2 && (!DIAG || ia1 < ja);
+            const f2 A2 = f2_make(ab0.x, ab1.x), nB2 = f2_make(ab0.y, ab1.y);
+            // FIXED64 keeps the library's k (q_i q_j) so that its integers match the
+            // other kernels; F32 uses (k q_i) q_j
+            const f2 kqq = MODE == MD_ACCUM_FIXED64 ? f2_mul(kc2, f2_mul(qi, f2_dup(pj.w)))
+                                                    : f2_mul(kcq, f2_dup(pj.w));
+            float y0, y1;
+            asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(r20));
+            asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y1) : "f"(r21));
+            const f2 y = f2_make(y0, y1);
+            const f2 ir = f2_mul(y, f2_fma(f2_mul(m05, r2), f2_mul(y, y), c15));
+            const f2 ir2 = f2_mul(ir, ir);
+            const f2 ir6 = f2_mul(f2_mul(ir2, ir2), ir2);
+            const f2 ir8 = f2_mul(ir6, ir2);
+            const f2 lj = f2_fma(A2, f2_mul(ir8, ir6), f2_mul(nB2, ir8));
+            float f0, f1;
+            f2_split(f2_fma(f2_mul(kqq, ir2), ir, lj), f0, f1);
+            f0 = ok0 ? f0 : 0.0f;
+            f1 = ok1 ? f1 : 0.0f;
+            const f2 f = f2_make(f0, f1);
+            const f2 fx = f2_mul(f, dx), fy = f2_mul(f, dy), fz = f2_mul(f, dz);
             Acc vx, vy, vz;  // reaction on ja (before the sign): this lane's two pairs
             if (MODE == MD_ACCUM_FIXED64) {
-                // the library's scalar pair arithmetic, pair by pair
-                float d0[3] = {p0.x - pj.x, p0.y - pj.y, p0.z - pj.z};
-                float d1[3] = {p1.x - pj.x, p1.y - pj.y, p1.z - pj.z};
-                if (SHIFT) {
-#pragma unroll
-                    for (int d = 0; d < 3; ++d) {
-                        d0[d] = d0[d] + k.lo[d];
-                        d1[d] = d1[d] + k.lo[d];
-                    }
-                }
-                const float r20 = pair_r2(d0[0], d0[1], d0[2]), r21 = pair_r2(d1[0], d1[1], d1[2]);
-                // padding sits at +-1e18: such pairs fail the cutoff test
-                const bool ok0 = r20 < k.rc2 && (!DIAG || ia0 < ja);
-                const bool ok1 = r21 < k.rc2 && (!DIAG || ia1 < ja);
-                const float kqq0 = __fmul_rn(k.kc, __fmul_rn(p0.w, pj.w));
-                const float kqq1 = __fmul_rn(k.kc, __fmul_rn(p1.w, pj.w));
-                float ir0, ir20, ir60, ir1, ir21, ir61;
-                float f0 = pair_f(r20, ab0.x, -ab0.y, kqq0, ir0, ir20, ir60);
-                float f1 = pair_f(r21, ab1.x, -ab1.y, kqq1, ir1, ir21, ir61);
-                f0 = ok0 ? f0 : 0.0f;
-                f1 = ok1 ? f1 : 0.0f;
-                Acc g0[3], g1[3];
-#pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    g0[d] = (Acc)(ok0 ? to_fixed(__fmul_rn(f0, d0[d]), k.status) : 0);
-                    g1[d] = (Acc)(ok1 ? to_fixed(__fmul_rn(f1, d1[d]), k.status) : 0);
-                }
-                ax0 += g0[0]; ay0 += g0[1]; az0 += g0[2];
-                ax1 += g1[0]; ay1 += g1[1]; az1 += g1[2];
-                vx = g0[0] + g1[0];
-                vy = g0[1] + g1[1];
-                vz = g0[2] + g1[2];
-                if (STATS >= kStatsCount) cnt += (unsigned)ok0 + (unsigned)ok1;
-                if (STATS == kStatsEnergy) {
-                    if (ok0) {
-                        e_lj += pair_u_lj(ab0.x, -ab0.y, ir60);
-                        e_c += kqq0 * ir0;
-                        vir += f0 * r20;
-                    }
-                    if (ok1) {
-                        e_lj += pair_u_lj(ab1.x, -ab1.y, ir61);
-                        e_c += kqq1 * ir1;
-                        vir += f1 * r21;
-                    }
-                }
+                float x0, x1, y0_, y1_, z0, z1;
+                f2_split(fx, x0, x1);
+                f2_split(fy, y0_, y1_);
+                f2_split(fz, z0, z1);
+                const Acc gx0 = (Acc)(ok0 ? to_fixed(x0, k.status) : 0), gx1 = (Acc)(ok1 ? to_fixed(x1, k.status) : 0);
+                const Acc gy0 = (Acc)(ok0 ? to_fixed(y0_, k.status) : 0), gy1 = (Acc)(ok1 ? to_fixed(y1_, k.status) : 0);
+                const Acc gz0 = (Acc)(ok0 ? to_fixed(z0, k.status) : 0), gz1 = (Acc)(ok1 ? to_fixed(z1, k.status) : 0);
+                ax0 += gx0; ay0 += gy0; az0 += gz0;
+                ax1 += gx1; ay1 += gy1; az1 += gz1;
+                vx = gx0 + gx1;
+                vy = gy0 + gy1;
+                vz = gz0 + gz1;
             } else {
-                f2 dx = f2_sub(xi, f2_dup(pj.x)), dy = f2_sub(yi, f2_dup(pj.y)), dz = f2_sub(zi, f2_dup(pj.z));
-                if (SHIFT) {
-                    dx = f2_add(dx, lox);
-                    dy = f2_add(dy, loy);
-                    dz = f2_add(dz, loz);
-                }
-                const f2 r2 = f2_fma(dz, dz, f2_fma(dy, dy, f2_mul(dx, dx)));
-                float r20, r21;
-                f2_split(r2, r20, r21);
-                // padding sits at +-1e18: such pairs fail the cutoff test
-                const bool ok0 = r20 < k.rc2 && (!DIAG || ia0 < ja);
-                const bool ok1 = r21 < k.rc2 && (!DIAG || ia1 < ja);
-                const f2 A2 = f2_make(ab0.x, ab1.x), nB2 = f2_make(ab0.y, ab1.y);
-                const f2 kqq = f2_mul(kcq, f2_dup(pj.w));
-                // pair_f, element by element: rsqrt_nr, the powers, Eq. 1 + Eq. 2
-                float y0, y1;
-                asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(r20));
-                asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y1) : "f"(r21));
-                const f2 y = f2_make(y0, y1);
-                const f2 ir = f2_mul(y, f2_fma(f2_mul(m05, r2), f2_mul(y, y), c15));
-                const f2 ir2 = f2_mul(ir, ir);
-                const f2 ir6 = f2_mul(f2_mul(ir2, ir2), ir2);
-                const f2 ir8 = f2_mul(ir6, ir2);
-                const f2 lj = f2_fma(A2, f2_mul(ir8, ir6), f2_mul(nB2, ir8));
-                const f2 cl = f2_mul(f2_mul(kqq, ir2), ir);
-                float f0, f1;
-                f2_split(f2_add(lj, cl), f0, f1);
-                f0 = ok0 ? f0 : 0.0f;
-                f1 = ok1 ? f1 : 0.0f;
-                const f2 f = f2_make(f0, f1);
-                const f2 fx = f2_mul(f, dx), fy = f2_mul(f, dy), fz = f2_mul(f, dz);
                 ax2 = f2_add(ax2, fx);
                 ay2 = f2_add(ay2, fy);
                 az2 = f2_add(az2, fz);
@@ -322,22 +294,22 @@ __device__ __forceinline__ void cluster_row(CluSmem<MODE> &sm, const float2 *s_a
                 vy = (Acc)(a0 + a1);
                 f2_split(fz, a0, a1);
                 vz = (Acc)(a0 + a1);
-                if (STATS >= kStatsCount) cnt += (unsigned)ok0 + (unsigned)ok1;
-                if (STATS == kStatsEnergy) {
-                    float i6a, i6b, ira, irb, ka, kb;
-                    f2_split(ir6, i6a, i6b);
-                    f2_split(ir, ira, irb);
-                    f2_split(kqq, ka, kb);
-                    if (ok0) {
-                        e_lj += pair_u_lj(ab0.x, -ab0.y, i6a);
-                        e_c += ka * ira;
-                        vir += f0 * r20;
-                    }
-                    if (ok1) {
-                        e_lj += pair_u_lj(ab1.x, -ab1.y, i6b);
-                        e_c += kb * irb;
-                        vir += f1 * r21;
-                    }
+            }
+            if (STATS >= kStatsCount) cnt += (unsigned)ok0 + (unsigned)ok1;
+            if (STATS == kStatsEnergy) {
+                float i6a, i6b, ira, irb, ka, kb;
+                f2_split(ir6, i6a, i6b);
+                f2_split(ir, ira, irb);
+                f2_split(kqq, ka, kb);
+                if (ok0) {
+                    e_lj += pair_u_lj(ab0.x, -ab0.y, i6a);
+                    e_c += ka * ira;
+                    vir += f0 * r20;
+                }
+                if (ok1) {
+                    e_lj += pair_u_lj(ab1.x, -ab1.y, i6b);
+                    e_c += kb * irb;
+                    vir += f1 * r21;
                 }
             }
 #pragma unroll

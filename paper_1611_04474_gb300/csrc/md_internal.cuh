@@ -144,7 +144,9 @@ __device__ __forceinline__ float rsqrt_nr(float x)
 }
 
 // Scalar f of F = f * r (Eq. 1: A/r^14 - B/r^8, Eq. 2: k q1 q2 / r^3); also returns
-// 1/r, 1/r^2, 1/r^6 for the energies.
+// 1/r, 1/r^2, 1/r^6 for the energies.  The Coulomb term joins the LJ term in one fused
+// multiply-add, so that no separate multiply feeds an add (which a compiler could fuse
+// in one kernel and not in another).
 __device__ __forceinline__ float pair_f(float r2, float A, float B, float kqq, float &ir,
                                         float &ir2, float &ir6)
 {
@@ -153,8 +155,7 @@ __device__ __forceinline__ float pair_f(float r2, float A, float B, float kqq, f
     ir6 = __fmul_rn(__fmul_rn(ir2, ir2), ir2);
     const float ir8 = __fmul_rn(ir6, ir2);
     const float lj = __fmaf_rn(A, __fmul_rn(ir8, ir6), -__fmul_rn(B, ir8));
-    const float cl = __fmul_rn(__fmul_rn(kqq, ir2), ir);
-    return __fadd_rn(lj, cl);
+    return __fmaf_rn(__fmul_rn(kqq, ir2), ir, lj);
 }
 
 __device__ __forceinline__ float pair_u_lj(float A, float B, float ir6)
