@@ -326,23 +326,29 @@ int md_step(double *pos, double *vel, void *forces, int32_t forces_valid, const 
     a.status = status;
 
     cudaError_t ce;
-    auto eval_forces = [&](bool energy) -> cudaError_t {
-        cudaError_t r = launch_build_cells(pq, type, n, box, cs, pm, pqs, tys, ws, wsp, status, s);
-        if (r != cudaSuccess) return r;
+    const double half_dt = 0.5 * dt_fs;
+    // the step's passes fused: [half kick +] drift + wrap + cell build in cluster order,
+    // then the forces with the second half kick in their last pass
+    a.presorted = 1;
+    a.kick_inv_mass = inv_mass;
+    a.kick_half_dt = half_dt;
+    auto build = [&](bool kick, double dt) -> cudaError_t {
+        return launch_kick_drift_build(pos, vel, forces, mode, inv_mass, q, type, n, box, nullptr, dt,
+                                       half_dt, kick, pq, cs, pm, pqs, tys, ws, wsp, status, s);
+    };
+    auto eval_forces = [&](bool energy, bool kick) -> cudaError_t {
         a.energy_virial_out = energy ? ev : nullptr;
+        a.kick_vel = kick ? vel : nullptr;
         return launch_forces(a, ws, wsp, s);
     };
     if (!forces_valid) {
         // wrap the start positions and make the float copy, then F(x0)
-        if ((ce = launch_drift_wrap(pos, vel, q, n, box, 0.0, pq, status, s)) != cudaSuccess) return MD_ERR_CUDA;
-        if ((ce = eval_forces(false)) != cudaSuccess) return MD_ERR_CUDA;
+        if ((ce = build(false, 0.0)) != cudaSuccess) return MD_ERR_CUDA;
+        if ((ce = eval_forces(false, false)) != cudaSuccess) return MD_ERR_CUDA;
     }
-    const double half_dt = 0.5 * dt_fs;
     for (int st = 0; st < n_steps; ++st) {
-        if ((ce = launch_kick(vel, forces, mode, inv_mass, n, half_dt, s)) != cudaSuccess) return MD_ERR_CUDA;
-        if ((ce = launch_drift_wrap(pos, vel, q, n, box, dt_fs, pq, status, s)) != cudaSuccess) return MD_ERR_CUDA;
-        if ((ce = eval_forces(energy_log != nullptr)) != cudaSuccess) return MD_ERR_CUDA;
-        if ((ce = launch_kick(vel, forces, mode, inv_mass, n, half_dt, s)) != cudaSuccess) return MD_ERR_CUDA;
+        if ((ce = build(true, dt_fs)) != cudaSuccess) return MD_ERR_CUDA;
+        if ((ce = eval_forces(energy_log != nullptr, true)) != cudaSuccess) return MD_ERR_CUDA;
         if (energy_log) {
             ce = launch_energy_log_row(vel, inv_mass, n, ev, energy_log + 4 * (size_t)st, ws, wsp, s);
             if (ce != cudaSuccess) return MD_ERR_CUDA;
@@ -467,6 +473,7 @@ int md_batch_step_tuned(int32_t nsys, const md_system_desc *systems, double *pos
     int32_t *tys = reinterpret_cast<int32_t *>(run + ws.st_type_sorted);
     float4 *pq = reinterpret_cast<float4 *>(run + ws.st_pos_q);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const double half_dt = 0.5 * dt_fs;
     ForceArgs a = {};
     a.cell_start = cs;
     a.perm = pm;
@@ -476,21 +483,25 @@ int md_batch_step_tuned(int32_t nsys, const md_system_desc *systems, double *pos
     a.mode = mode;
     a.forces_out = forces;
     a.status = status;
-    auto eval_forces = [&]() -> cudaError_t {
-        cudaError_t r = launch_build_cells_batched(pq, type, b, cs, pm, pqs, tys, ws, run, status, s);
-        if (r != cudaSuccess) return r;
+    // the same fused passes as md_step, over the whole batch
+    a.presorted = 1;
+    a.kick_inv_mass = inv_mass;
+    a.kick_half_dt = half_dt;
+    auto build = [&](bool kick, double dt) -> cudaError_t {
+        return launch_kick_drift_build(pos, vel, forces, mode, inv_mass, q, type, bl.n, BoxF{}, &b, dt,
+                                       half_dt, kick, pq, cs, pm, pqs, tys, ws, run, status, s);
+    };
+    auto eval_forces = [&](bool kick) -> cudaError_t {
+        a.kick_vel = kick ? vel : nullptr;
         return launch_forces_batched(a, b, pair_count, ws, run, s, shape_reg, shape_mi);
     };
     if (!forces_valid) {
-        if (launch_drift_wrap_batched(pos, vel, q, b, 0.0, pq, status, s) != cudaSuccess) return MD_ERR_CUDA;
-        if (eval_forces() != cudaSuccess) return MD_ERR_CUDA;
+        if (build(false, 0.0) != cudaSuccess) return MD_ERR_CUDA;
+        if (eval_forces(false) != cudaSuccess) return MD_ERR_CUDA;
     }
-    const double half_dt = 0.5 * dt_fs;
     for (int st = 0; st < n_steps; ++st) {
-        if (launch_kick(vel, forces, mode, inv_mass, bl.n, half_dt, s) != cudaSuccess) return MD_ERR_CUDA;
-        if (launch_drift_wrap_batched(pos, vel, q, b, dt_fs, pq, status, s) != cudaSuccess) return MD_ERR_CUDA;
-        if (eval_forces() != cudaSuccess) return MD_ERR_CUDA;
-        if (launch_kick(vel, forces, mode, inv_mass, bl.n, half_dt, s) != cudaSuccess) return MD_ERR_CUDA;
+        if (build(true, dt_fs) != cudaSuccess) return MD_ERR_CUDA;
+        if (eval_forces(true) != cudaSuccess) return MD_ERR_CUDA;
     }
     return MD_OK;
 }

@@ -232,6 +232,11 @@ cudaError_t launch_forces(const ForceArgs &a, const WsLayout &ws, char *wsp, cud
     if (a.energy_virial_out || a.pair_count_out)
         k_reduce_partials<<<1, 256, 0, stream>>>(partials, nblocks, a.energy_virial_out,
                                                  a.pair_count_out);
+    // the half kick of an MD step: inside the cluster kernel's finalize, else here
+    if (a.kick_vel && algo != MD_ALGO_CLUSTER) {
+        cudaError_t e = launch_kick(a.kick_vel, a.forces_out, a.mode, a.kick_inv_mass, a.n, a.kick_half_dt, stream);
+        if (e != cudaSuccess) return e;
+    }
     return cudaGetLastError();
 }
 

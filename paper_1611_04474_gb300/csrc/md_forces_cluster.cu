@@ -53,18 +53,15 @@ constexpr int kStatsNone = 0;    // forces only
 constexpr int kStatsCount = 1;   // + within-cutoff pair count
 constexpr int kStatsEnergy = 2;  // + count, energies and virial
 // Per cell: sort its atoms by (column, z along the column) and write the reordered
-// copies.  corder[k] is the sorted-order slot of cluster-order slot k.  BATCHED: cells
-// are numbered over the batch and each takes its system's box.
-template <bool BATCHED>
+// copies.  corder[k] is the sorted-order slot of cluster-order slot k.  (The MD steps
+// build their cells in this order directly: k_sort_cluster.)
 __global__ void __launch_bounds__(kOrderThreads)
 k_cluster_order(const int32_t *__restrict__ cell_start, const float4 *__restrict__ pq,
-                const int32_t *__restrict__ ty, BoxF box_in, BatchArgs bt,
-                float4 *__restrict__ cpq, int32_t *__restrict__ cty, int32_t *__restrict__ corder)
+                const int32_t *__restrict__ ty, BoxF box, float4 *__restrict__ cpq,
+                int32_t *__restrict__ cty, int32_t *__restrict__ corder)
 {
     __shared__ unsigned long long s_key[kSortMax];
-    const int cg = blockIdx.x;
-    const BoxF &box = BATCHED ? bt.sys[bt.cell_sys[cg]].box : box_in;
-    const int c = BATCHED ? cg - bt.sys[bt.cell_sys[cg]].cell_offset : cg;
+    const int cg = blockIdx.x, c = cg;
     const int b = cell_start[cg], m = cell_start[cg + 1] - b;
     if (m <= 0) return;
     if (m > kSortMax) {
@@ -549,22 +546,30 @@ k_cluster(CluArgs a, BatchArgs bt, unsigned long long *sys_pair_count)
     }
 }
 
-// Cluster-order accumulators -> forces_out in input order.
-template <int MODE>
+// Cluster-order accumulators -> forces_out in input order (slot s holds the atom
+// perm[corder[s]], or perm[s] without corder).  KICK: the half kick v += dt/2 a(F) of
+// that atom in the same pass, with the arithmetic of k_kick.
+template <int MODE, bool KICK>
 __global__ void __launch_bounds__(256)
 k_finalize_clu(const void *__restrict__ accum, const int32_t *__restrict__ corder,
                const int32_t *__restrict__ perm, int n, void *__restrict__ forces_out,
-               uint32_t *status)
+               uint32_t *status, double *__restrict__ vel, const float *__restrict__ inv_mass,
+               double half_dt)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
-    const int o = perm[corder[s]];
+    const int o = perm[corder ? corder[s] : s];
+    double f[3];
     if (MODE == MD_ACCUM_FIXED64) {
         const long long *acc = static_cast<const long long *>(accum);
         long long *F = static_cast<long long *>(forces_out);
-        F[3 * o + 0] = acc[s];
-        F[3 * o + 1] = acc[(size_t)n + s];
-        F[3 * o + 2] = acc[2 * (size_t)n + s];
+        const long long v[3] = {acc[s], acc[(size_t)n + s], acc[2 * (size_t)n + s]};
+        const double sc = 1.0 / 4294967296.0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            F[3 * o + k] = v[k];
+            f[k] = (double)v[k] * sc;
+        }
     } else {
         const float4 v = static_cast<const float4 *>(accum)[s];
         float *F = static_cast<float *>(forces_out);
@@ -572,6 +577,14 @@ k_finalize_clu(const void *__restrict__ accum, const int32_t *__restrict__ corde
         F[3 * o + 1] = v.y;
         F[3 * o + 2] = v.z;
         if (!isfinite(v.x + v.y + v.z)) set_status(status, MD_STATUS_NONFINITE);
+        f[0] = v.x;
+        f[1] = v.y;
+        f[2] = v.z;
+    }
+    if (KICK) {
+        const double im = (double)inv_mass[o];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) vel[3 * o + k] = kick_velocity(vel[3 * o + k], f[k], im, half_dt);
     }
 }
 
@@ -604,12 +617,13 @@ cudaError_t launch_cluster(const ForceArgs &a, const WsLayout &ws, char *wsp, Pa
     int32_t *corder = reinterpret_cast<int32_t *>(wsp + ws.clu_order);
     cudaError_t e = cudaMemsetAsync(accum, 0, acc_bytes, stream);
     if (e != cudaSuccess) return e;
-    k_cluster_order<false><<<a.box.ncell, kOrderThreads, 0, stream>>>(
-        a.cell_start, a.pos_q_sorted, a.type_sorted, a.box, BatchArgs{}, cpq, cty, corder);
+    if (!a.presorted)
+        k_cluster_order<<<a.box.ncell, kOrderThreads, 0, stream>>>(a.cell_start, a.pos_q_sorted,
+                                                                   a.type_sorted, a.box, cpq, cty, corder);
     CluArgs c;
     c.cell_start = a.cell_start;
-    c.pq = cpq;
-    c.ty = cty;
+    c.pq = a.presorted ? a.pos_q_sorted : cpq;
+    c.ty = a.presorted ? a.type_sorted : cty;
     c.box = a.box;
     c.AB = a.AB;
     c.ntypes = a.ntypes;
@@ -621,47 +635,31 @@ cudaError_t launch_cluster(const ForceArgs &a, const WsLayout &ws, char *wsp, Pa
     c.status = a.status;
     dim3 grid(a.box.ncell, 14);
     const int stats = a.energy_virial_out ? kStatsEnergy : (a.pair_count_out ? kStatsCount : kStatsNone);
-    const int g = (a.n + 255) / 256;
     if (a.mode == MD_ACCUM_FIXED64) {
         if (stats == kStatsEnergy) launch_cluster_t<MD_ACCUM_FIXED64, kStatsEnergy>(c, grid, stream);
         else if (stats == kStatsCount) launch_cluster_t<MD_ACCUM_FIXED64, kStatsCount>(c, grid, stream);
         else launch_cluster_t<MD_ACCUM_FIXED64, kStatsNone>(c, grid, stream);
-        k_finalize_clu<MD_ACCUM_FIXED64><<<g, 256, 0, stream>>>(accum, corder, a.perm, a.n, a.forces_out, a.status);
     } else {
         if (stats == kStatsEnergy) launch_cluster_t<MD_ACCUM_F32, kStatsEnergy>(c, grid, stream);
         else if (stats == kStatsCount) launch_cluster_t<MD_ACCUM_F32, kStatsCount>(c, grid, stream);
         else launch_cluster_t<MD_ACCUM_F32, kStatsNone>(c, grid, stream);
-        k_finalize_clu<MD_ACCUM_F32><<<g, 256, 0, stream>>>(accum, corder, a.perm, a.n, a.forces_out, a.status);
     }
     *nblocks_out = a.box.ncell * 14;
-    return cudaGetLastError();
-}
-
-// Batched: cluster order of every cell of the batch (all systems), so that both force
-// launches (cluster kernel for the regular systems, half-shell kernel for the 2-cell
-// boxes) read cluster-ordered tiles and accumulate in cluster order.
-cudaError_t launch_cluster_order_batched(const ForceArgs &a, const BatchArgs &b, const WsLayout &ws,
-                                         char *wsp, cudaStream_t stream)
-{
-    if (b.ncell <= 0) return cudaSuccess;
-    k_cluster_order<true><<<b.ncell, kOrderThreads, 0, stream>>>(
-        a.cell_start, a.pos_q_sorted, a.type_sorted, BoxF{}, b,
-        reinterpret_cast<float4 *>(wsp + ws.clu_pos_q), reinterpret_cast<int32_t *>(wsp + ws.clu_type),
-        reinterpret_cast<int32_t *>(wsp + ws.clu_order));
-    return cudaGetLastError();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return launch_finalize_cluster(a, accum, ws, wsp, a.n, stream);
 }
 
 // Batched cluster kernel over the regular systems' cells (b.cell_list[0 .. ncell_reg)).
 cudaError_t launch_cluster_batched(int mode, const BatchArgs &b, const int32_t *cell_start,
-                                   void *accum, Partial *partials, uint32_t *status,
-                                   unsigned long long *sys_pair_count, const WsLayout &ws,
-                                   char *wsp, cudaStream_t stream)
+                                   const float4 *pq, const int32_t *ty, void *accum,
+                                   Partial *partials, uint32_t *status,
+                                   unsigned long long *sys_pair_count, cudaStream_t stream)
 {
     if (b.ncell_reg <= 0) return cudaSuccess;
     CluArgs c = {};
     c.cell_start = cell_start;
-    c.pq = reinterpret_cast<const float4 *>(wsp + ws.clu_pos_q);
-    c.ty = reinterpret_cast<const int32_t *>(wsp + ws.clu_type);
+    c.pq = pq;  // cluster-ordered tiles
+    c.ty = ty;
     c.ntypes = b.max_ntypes;  // sizes the shared LJ table
     c.accum = accum;
     c.n = b.n;
@@ -678,18 +676,26 @@ cudaError_t launch_cluster_batched(int mode, const BatchArgs &b, const int32_t *
     return cudaGetLastError();
 }
 
-// Cluster-order accumulators -> forces in input order (batched or not).
-cudaError_t launch_finalize_cluster(int mode, const void *accum, const WsLayout &ws, char *wsp,
-                                    const int32_t *perm, int n, void *forces_out, uint32_t *status,
-                                    cudaStream_t stream)
+// Cluster-order accumulators -> forces in input order (batched or not), with the half
+// kick when a.kick_vel is set.
+cudaError_t launch_finalize_cluster(const ForceArgs &a, const void *accum, const WsLayout &ws,
+                                    char *wsp, int n, cudaStream_t stream)
 {
     if (n <= 0) return cudaSuccess;
-    const int32_t *corder = reinterpret_cast<const int32_t *>(wsp + ws.clu_order);
+    const int32_t *corder = a.presorted ? nullptr : reinterpret_cast<const int32_t *>(wsp + ws.clu_order);
     const int g = (n + 255) / 256;
-    if (mode == MD_ACCUM_FIXED64)
-        k_finalize_clu<MD_ACCUM_FIXED64><<<g, 256, 0, stream>>>(accum, corder, perm, n, forces_out, status);
-    else
-        k_finalize_clu<MD_ACCUM_F32><<<g, 256, 0, stream>>>(accum, corder, perm, n, forces_out, status);
+    const bool kick = a.kick_vel != nullptr;
+    if (a.mode == MD_ACCUM_FIXED64) {
+        if (kick)
+            k_finalize_clu<MD_ACCUM_FIXED64, true><<<g, 256, 0, stream>>>(accum, corder, a.perm, n, a.forces_out, a.status, a.kick_vel, a.kick_inv_mass, a.kick_half_dt);
+        else
+            k_finalize_clu<MD_ACCUM_FIXED64, false><<<g, 256, 0, stream>>>(accum, corder, a.perm, n, a.forces_out, a.status, nullptr, nullptr, 0.0);
+    } else {
+        if (kick)
+            k_finalize_clu<MD_ACCUM_F32, true><<<g, 256, 0, stream>>>(accum, corder, a.perm, n, a.forces_out, a.status, a.kick_vel, a.kick_inv_mass, a.kick_half_dt);
+        else
+            k_finalize_clu<MD_ACCUM_F32, false><<<g, 256, 0, stream>>>(accum, corder, a.perm, n, a.forces_out, a.status, nullptr, nullptr, 0.0);
+    }
     return cudaGetLastError();
 }
 

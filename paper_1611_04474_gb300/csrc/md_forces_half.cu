@@ -575,13 +575,13 @@ cudaError_t launch_forces_batched(const ForceArgs &a, const BatchArgs &b,
     void *accum = wsp + ws.accum;
     cudaError_t e = cudaMemsetAsync(accum, 0, acc_bytes, stream);
     if (e != cudaSuccess) return e;
-    // every cell in cluster order; both launches read those copies and accumulate in
-    // cluster order
-    if ((e = launch_cluster_order_batched(a, b, ws, wsp, stream)) != cudaSuccess) return e;
+    // the batch's cells come from the fused MD-step build, already in cluster order;
+    // both launches read them and accumulate in that order
+    if (!a.presorted) return cudaErrorInvalidValue;
     HalfArgs h = {};
     h.cell_start = a.cell_start;
-    h.pq = reinterpret_cast<const float4 *>(wsp + ws.clu_pos_q);
-    h.ty = reinterpret_cast<const int32_t *>(wsp + ws.clu_type);
+    h.pq = a.pos_q_sorted;
+    h.ty = a.type_sorted;
     h.accum = accum;
     h.n = b.n;
     h.status = a.status;
@@ -592,8 +592,8 @@ cudaError_t launch_forces_batched(const ForceArgs &a, const BatchArgs &b,
         h.partials = partials;
         dim3 grid(b.ncell_reg, 14);
         if (shape_reg == 0)
-            e = launch_cluster_batched(a.mode, b, a.cell_start, accum, partials, a.status, sys_pair_count,
-                                       ws, wsp, stream);
+            e = launch_cluster_batched(a.mode, b, a.cell_start, h.pq, h.ty, accum, partials, a.status,
+                                       sys_pair_count, stream);
         else if (a.mode == MD_ACCUM_FIXED64) launch_batched_shape<MD_ACCUM_FIXED64, false>(shape_reg, h, grid, stream, b, sys_pair_count);
         else launch_batched_shape<MD_ACCUM_F32, false>(shape_reg, h, grid, stream, b, sys_pair_count);
         if (e != cudaSuccess) return e;
@@ -604,9 +604,7 @@ cudaError_t launch_forces_batched(const ForceArgs &a, const BatchArgs &b,
         if (a.mode == MD_ACCUM_FIXED64) launch_batched_shape<MD_ACCUM_FIXED64, true>(shape_mi, h, grid, stream, b, sys_pair_count);
         else launch_batched_shape<MD_ACCUM_F32, true>(shape_mi, h, grid, stream, b, sys_pair_count);
     }
-    if ((e = launch_finalize_cluster(a.mode, accum, ws, wsp, a.perm, b.n, a.forces_out, a.status, stream)) !=
-        cudaSuccess)
-        return e;
+    if ((e = launch_finalize_cluster(a, accum, ws, wsp, b.n, stream)) != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

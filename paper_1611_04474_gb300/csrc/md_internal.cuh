@@ -106,6 +106,83 @@ __device__ __forceinline__ int cell_coord(double w, int nc, double inv_edge)
     return f < 0.0 ? 0 : (f > (double)(nc - 1) ? nc - 1 : (int)f);
 }
 
+__device__ __forceinline__ bool finite3(double x, double y, double z)
+{
+    return isfinite(x) && isfinite(y) && isfinite(z);
+}
+
+// Cell of a float position under the documented rule (FP64 wrap of the float value,
+// floor(w * n/L) clamped); a non-finite coordinate sets the status and gives cell 0.
+__device__ __forceinline__ int cell_of(const float4 &p, const BoxF &box, uint32_t *status)
+{
+    double x = p.x, y = p.y, z = p.z;
+    if (!finite3(x, y, z)) {
+        set_status(status, MD_STATUS_NONFINITE);
+        return 0;
+    }
+    int cx = cell_coord(wrap_coord(x, box.L[0]), box.dims[0], box.inv_edge[0]);
+    int cy = cell_coord(wrap_coord(y, box.L[1]), box.dims[1], box.inv_edge[1]);
+    int cz = cell_coord(wrap_coord(z, box.L[2]), box.dims[2], box.inv_edge[2]);
+    return cx + box.dims[0] * (cy + box.dims[1] * cz);
+}
+
+// Velocity-Verlet updates with every rounding spelled out (no contraction), in the
+// oracle's order: v + ((dt/2 F) (1/m)) 4.184e-4 and x + dt v.  Every kernel that moves
+// atoms uses these, so the single-system and batched steps agree bit for bit.
+__device__ __forceinline__ double kick_velocity(double v, double f, double im, double half_dt)
+{
+    return __dadd_rn(v, __dmul_rn(__dmul_rn(__dmul_rn(half_dt, f), im), kAccelPerForcePerMass));
+}
+__device__ __forceinline__ double drift_coord(double x, double v, double dt)
+{
+    return __dadd_rn(x, __dmul_rn(dt, v));
+}
+
+// Sorted-order slot of one atom: its input index, its wrapped float position and
+// charge, its type (the outputs of the cell build).
+__device__ __forceinline__ void place(int e, int slot, const float4 *__restrict__ pos_q,
+                                      const int32_t *__restrict__ type, const BoxF &box,
+                                      int32_t *__restrict__ perm, float4 *__restrict__ pos_q_sorted,
+                                      int32_t *__restrict__ type_sorted)
+{
+    perm[slot] = e;
+    const float4 p = pos_q[e];
+    const double x = p.x, y = p.y, z = p.z;
+    float4 o;
+    if (isfinite(x) && isfinite(y) && isfinite(z)) {
+        o.x = (float)wrap_coord(x, box.L[0]);
+        o.y = (float)wrap_coord(y, box.L[1]);
+        o.z = (float)wrap_coord(z, box.L[2]);
+    } else {
+        o.x = o.y = o.z = 0.0f;
+    }
+    o.w = p.w;
+    pos_q_sorted[slot] = o;
+    type_sorted[slot] = type[e];
+}
+
+// Force on atom i as FP64 from the forces array of a mode (input order).
+__device__ __forceinline__ void load_force(const void *forces, int mode, int i, double f[3])
+{
+    if (mode == MD_ACCUM_F32) {
+        const float *F = static_cast<const float *>(forces);
+        f[0] = F[3 * i];
+        f[1] = F[3 * i + 1];
+        f[2] = F[3 * i + 2];
+    } else if (mode == MD_ACCUM_FIXED64) {
+        const long long *F = static_cast<const long long *>(forces);
+        const double s = 1.0 / 4294967296.0;
+        f[0] = (double)F[3 * i] * s;
+        f[1] = (double)F[3 * i + 1] * s;
+        f[2] = (double)F[3 * i + 2] * s;
+    } else {
+        const double *F = static_cast<const double *>(forces);
+        f[0] = F[3 * i];
+        f[1] = F[3 * i + 1];
+        f[2] = F[3 * i + 2];
+    }
+}
+
 // Minimum-image displacement xi - xj along one axis in FP32 for coordinates in
 // [0, L].  The image is chosen from the rounded difference, then the difference is
 // formed again so that it is exact up to one rounding of the result: the box shift
@@ -250,6 +327,13 @@ struct ForceArgs {
     double *energy_virial_out;
     unsigned long long *pair_count_out;
     uint32_t *status;
+    // within-cell order already the cluster kernel's (from the fused MD-step build):
+    // no ordering pass, perm maps each slot to its input index
+    int presorted = 0;
+    // optional half kick v += dt/2 a(F) applied as the forces are written (MD step)
+    double *kick_vel = nullptr;
+    const float *kick_inv_mass = nullptr;
+    double kick_half_dt = 0.0;
 };
 
 cudaError_t launch_forces(const ForceArgs &a, const WsLayout &ws, char *wsp, cudaStream_t stream);
@@ -258,9 +342,8 @@ void cutoff_thresholds(const BoxF &box, double rc, bool mi, float *rc2, float *r
 cudaError_t launch_half_shell(const ForceArgs &a, const WsLayout &ws, char *wsp, Partial *partials,
                               int *nblocks_out, cudaStream_t stream);
 bool cluster_kernel_applies(const BoxF &box);
-cudaError_t launch_finalize_cluster(int mode, const void *accum, const WsLayout &ws, char *wsp,
-                                    const int32_t *perm, int n, void *forces_out, uint32_t *status,
-                                    cudaStream_t stream);
+cudaError_t launch_finalize_cluster(const ForceArgs &a, const void *accum, const WsLayout &ws,
+                                    char *wsp, int n, cudaStream_t stream);
 cudaError_t launch_cluster(const ForceArgs &a, const WsLayout &ws, char *wsp, Partial *partials,
                            int *nblocks_out, cudaStream_t stream);
 
@@ -273,28 +356,22 @@ struct BatchArgs {
     int nsys, n, ncell, ncell_mi, ncell_reg;
     int max_ntypes;  // largest LJ table of the batch: sizes the kernels' shared copy
 };
-cudaError_t launch_cluster_order_batched(const ForceArgs &a, const BatchArgs &b, const WsLayout &ws,
-                                         char *wsp, cudaStream_t stream);
 cudaError_t launch_cluster_batched(int mode, const BatchArgs &b, const int32_t *cell_start,
-                                   void *accum, Partial *partials, uint32_t *status,
-                                   unsigned long long *sys_pair_count, const WsLayout &ws,
-                                   char *wsp, cudaStream_t stream);
-cudaError_t launch_build_cells_batched(const float4 *pos_q, const int32_t *type, const BatchArgs &b,
-                                       int32_t *cell_start, int32_t *perm, float4 *pos_q_sorted,
-                                       int32_t *type_sorted, const WsLayout &ws, char *wsp,
-                                       uint32_t *status, cudaStream_t stream);
+                                   const float4 *pq, const int32_t *ty, void *accum,
+                                   Partial *partials, uint32_t *status,
+                                   unsigned long long *sys_pair_count, cudaStream_t stream);
+cudaError_t launch_kick_drift_build(double *pos, double *vel, const void *forces, int mode,
+                                    const float *inv_mass, const float *q, const int32_t *type, int n,
+                                    const BoxF &box_in, const BatchArgs *b, double dt, double half_dt,
+                                    bool kick, float4 *pos_q, int32_t *cell_start, int32_t *perm,
+                                    float4 *pos_q_sorted, int32_t *type_sorted, const WsLayout &ws,
+                                    char *wsp, uint32_t *status, cudaStream_t stream);
 cudaError_t launch_forces_batched(const ForceArgs &a, const BatchArgs &b,
                                   unsigned long long *sys_pair_count, const WsLayout &ws,
                                   char *wsp, cudaStream_t stream, int shape_reg, int shape_mi);
-cudaError_t launch_drift_wrap_batched(double *pos, const double *vel, const float *q, const BatchArgs &b,
-                                      double dt, float4 *pos_q_out, uint32_t *status,
-                                      cudaStream_t stream);
 
 cudaError_t launch_kick(double *vel, const void *forces, int mode, const float *inv_mass, int n,
                         double half_dt, cudaStream_t stream);
-cudaError_t launch_drift_wrap(double *pos, const double *vel, const float *q, int n,
-                              const BoxF &box, double dt, float4 *pos_q_out, uint32_t *status,
-                              cudaStream_t stream);
 cudaError_t launch_energy_log_row(const double *vel, const float *inv_mass, int n,
                                   const double *energy_virial, double *row, const WsLayout &ws,
                                   char *wsp, cudaStream_t stream);
