@@ -34,7 +34,8 @@ def main(argv=None):
     res = srv.run(jobs)
     res.update({"mode": args.mode, "rate": args.rate, "tick_steps": args.tick,
                 "ticks": srv.ticks, "rebuilds": srv.rebuilds,
-                "max_footprint_gb": srv.max_footprint / (1 << 30)})
+                "max_footprint_gb": srv.max_footprint / (1 << 30),
+                "loop_seconds": {k: round(v, 3) for k, v in srv.seconds.items()}})
     # stand-alone times on a sample of jobs, fitted as a + b * pairs
     rng = np.random.default_rng(0)
     sample = rng.choice(len(jobs), size=min(args.alone_sample, len(jobs)), replace=False)

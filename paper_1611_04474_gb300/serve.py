@@ -18,6 +18,7 @@ from __future__ import annotations
 
 import collections
 import math
+import threading
 import time
 from dataclasses import dataclass, field
 
@@ -52,24 +53,42 @@ class Job:
     system: object = None
     ff: object = None
     state: dict = field(default_factory=dict)
+    ready: threading.Event = field(default_factory=threading.Event)  # system received
 
 
 class Server:
     def __init__(self, mode=api.ACCUM_FIXED64, budget_bytes: int = 16 << 30, tick_steps: int = 10,
-                 dt_fs: float = 1.0, device="cuda"):
+                 dt_fs: float = 1.0, device="cuda", lookahead: int = 32):
         self.mode = mode
         self.budget = int(budget_bytes)
         self.tick = int(tick_steps)
         self.dt = float(dt_fs)
         self.device = torch.device(device)
+        self.lookahead = int(lookahead)
         self.max_footprint = 0
         self.ticks = 0
         self.rebuilds = 0
+        # wall seconds of the serving loop by phase
+        self.seconds = {"upload": 0.0, "rebuild": 0.0, "ticks": 0.0, "write_back": 0.0}
 
     # ---------------------------------------------------------------- job state
+    def _receive(self, ordered, admitted_count, stop):
+        """The request bodies: each job's system is materialised on the host off the
+        serving loop, in arrival order, at most `lookahead` jobs ahead of admission (what
+        a client upload would deliver with the request)."""
+        for k, j in enumerate(ordered):
+            with admitted_count:
+                while k >= admitted_count.n + self.lookahead and not stop.is_set():
+                    admitted_count.wait(0.05)
+            if stop.is_set():
+                return
+            j.system = j.make_system()
+            j.ready.set()
+
     def _load(self, j: Job):
-        s = j.make_system()
-        j.system = s
+        if not j.ready.is_set():
+            j.ready.wait()
+        s = j.system
         j.ff = api.ForceField.from_system(s, self.device)
         d = self.device
         j.state = {
@@ -82,27 +101,51 @@ class Server:
         }
         j.remaining = j.n_steps
 
-    def _arena(self, active):
+    def _arena(self, active, prev=None, prev_active=()):
+        """A batch over `active`: jobs that were in the previous arena bring their
+        current state straight from it (device to device), new jobs from their own."""
+        where = {id(j): k for k, j in enumerate(prev_active)}
         keys = ("pos", "vel", "forces", "q", "types", "inv_mass")
-        state = {k: torch.cat([j.state[k] for j in active]).contiguous() for k in keys}
+
+        def src(j, key):
+            k = where.get(id(j))
+            return j.state[key] if k is None else getattr(prev, key)[prev.system_slice(k)]
+        state = {key: torch.cat([src(j, key) for j in active]).contiguous() for key in keys}
         return api.Batch([j.system for j in active], mode=self.mode, device=self.device,
                          state=state, ffs=[j.ff for j in active])
 
-    def _write_back(self, batch, active):
+    def _write_back(self, batch, active, jobs):
+        """The current state of `jobs` (a subset of `active`) into their own tensors."""
         for k, j in enumerate(active):
-            sl = batch.system_slice(k)
-            for key in ("pos", "vel", "forces"):
-                j.state[key].copy_(getattr(batch, key)[sl])
+            if any(j is x for x in jobs):
+                sl = batch.system_slice(k)
+                for key in ("pos", "vel", "forces"):
+                    j.state[key].copy_(getattr(batch, key)[sl])
 
     # ---------------------------------------------------------------- main loop
     def run(self, jobs, realtime: bool = True):
         """Serve `jobs` (list of Job) until all have finished; returns a stats dict.
         realtime: jobs become visible at their arrival times on the wall clock."""
         pending = collections.deque(sorted(jobs, key=lambda j: j.arrival))
+        admitted_count = threading.Condition()
+        admitted_count.n = 0
+        stop = threading.Event()
+        receiver = threading.Thread(target=self._receive, args=(list(pending), admitted_count, stop),
+                                    daemon=True)
+        receiver.start()
+        try:
+            return self._serve(pending, admitted_count, realtime)
+        finally:
+            stop.set()
+            receiver.join()
+
+    def _serve(self, pending, admitted_count, realtime):
+        jobs = list(pending)
         queue = collections.deque()
         active = []
         footprint = 0
         batch = None
+        in_batch = []  # the jobs of `batch`, in its order
         changed = True
         t0 = time.perf_counter()
         now = lambda: time.perf_counter() - t0  # noqa: E731
@@ -112,7 +155,12 @@ class Server:
                 queue.append(pending.popleft())
             while queue and footprint + job_footprint_bytes(queue[0].n_atoms) <= self.budget:
                 j = queue.popleft()
+                t1 = time.perf_counter()
                 self._load(j)
+                self.seconds["upload"] += time.perf_counter() - t1
+                with admitted_count:
+                    admitted_count.n += 1
+                    admitted_count.notify_all()
                 j.admitted = now()
                 active.append(j)
                 footprint += job_footprint_bytes(j.n_atoms)
@@ -125,14 +173,19 @@ class Server:
                     time.sleep(max(0.0, pending[0].arrival - now()))
                 continue
             if changed:
-                batch = self._arena(active)
+                t1 = time.perf_counter()
+                batch = self._arena(active, batch, in_batch)
+                in_batch = list(active)
                 batch.step(0)  # forces of the current positions (first call: not yet valid)
                 self.rebuilds += 1
                 changed = False
+                self.seconds["rebuild"] += time.perf_counter() - t1
             k = min(self.tick, min(j.remaining for j in active))
+            t1 = time.perf_counter()
             batch.pair_count.zero_()
             batch.step(k, dt_fs=self.dt, count_pairs=True)
             counts = batch.pair_count.cpu().numpy()  # waits for the tick
+            self.seconds["ticks"] += time.perf_counter() - t1
             self.ticks += 1
             t = now()
             done = []
@@ -147,7 +200,9 @@ class Server:
             head = queue[0] if queue else (pending[0] if pending and realtime and pending[0].arrival <= now() else None)
             joinable = head is not None and footprint - freed + job_footprint_bytes(head.n_atoms) <= self.budget
             if done or joinable:
-                self._write_back(batch, active)
+                t1 = time.perf_counter()
+                self._write_back(batch, active, done)
+                self.seconds["write_back"] += time.perf_counter() - t1
                 for j in done:
                     j.finished = t
                     active.remove(j)
