@@ -120,3 +120,37 @@ def test_autotuner_leaves_the_trajectory_and_caches(cuda_lib, tmp_path):
     again = api.Batch(systems, mode=api.ACCUM_FIXED64)
     e2 = autotune.tune(again, cache_path=cache)
     assert not e2["measured"] and tuple(e2["tuning"]) == tuple(e1["tuning"]) == again.tuning
+
+
+def test_full_size_batch_sampled(cuda_lib):
+    """The 256-system batch (1.24 M atoms, N 500-20,000) at full size: FIXED64 steps of
+    sampled systems bitwise equal to running them alone, FP32 forces of sampled systems
+    against the oracle."""
+    api = cuda_lib
+    systems = W.batch_of_systems()
+    b = api.Batch(systems, mode=api.ACCUM_FIXED64)
+    b.step(2, dt_fs=1.0)
+    torch.cuda.synchronize()
+    assert int(b.status.item()) == 0
+    sizes = np.array([s.n for s in systems])
+    dims = [np.floor(s.box / s.rc).min() for s in systems]
+    picks = {int(np.argmax(sizes)), int(np.argmin(sizes)), int(np.argmax(dims)),
+             int(np.argmin(dims)), 100}
+    Xb, Fb = b.pos.cpu().numpy(), b.forces.cpu().numpy()
+    for k in sorted(picks):
+        eng = _alone(api, systems[k], api.ACCUM_FIXED64, 2)
+        sl = b.system_slice(k)
+        assert np.array_equal(Xb[sl], eng.pos.cpu().numpy()), k
+        assert np.array_equal(Fb[sl], eng.forces.cpu().numpy()), k
+    b32 = api.Batch(systems, mode=api.ACCUM_F32)
+    b32.step(0)
+    torch.cuda.synchronize()
+    F32 = b32.forces.cpu().numpy().astype(np.float64)
+    for k in sorted(picks):
+        s = systems[k]
+        ff = oracle.ForceField.from_system(s)
+        p = s.pos.astype(np.float64)
+        ref = oracle.forces_cells(p, s.q, s.type, s.box, ff)
+        alts, nb = boundary_alternatives(p, s, ff, ref.F)
+        err = force_errors(F32[b32.system_slice(k)], ref.F, ref.cond, alts)
+        assert err["max_norm"] <= 1e-5, (k, err)

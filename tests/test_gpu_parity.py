@@ -283,3 +283,59 @@ def test_errors_from_the_abi(cuda_lib):
     with pytest.raises(api.MDError) as e:
         api.nonbonded_forces(eng.cells, eng.box, ff_bad, eng.workspace)
     assert e.value.code == -2
+
+
+# ------------------------------------------------------------------ full sizes
+
+def _boundary_atoms(p, box, rc, sel):
+    """Sampled atoms with a partner whose FP64 r^2 lies in the boundary window of rc^2."""
+    from scipy.spatial import cKDTree
+
+    from tests.parity import boundary_window
+
+    w = np.mod(p, box)
+    tree = cKDTree(w, boxsize=box)
+    lo, hi = rc * rc - boundary_window(rc), rc * rc + boundary_window(rc)
+    out = np.zeros(len(sel), bool)
+    for k, i in enumerate(sel):
+        for j in tree.query_ball_point(w[i], np.sqrt(hi)):
+            if j == i:
+                continue
+            d = p[i] - p[j]
+            d -= box * np.round(d / box)
+            r2 = float(d @ d)
+            if lo <= r2 <= hi:
+                out[k] = True
+                break
+    return out
+
+
+def _largest_reference():
+    """The 1,475,584-atom lattice, 2,048 sampled atoms, their oracle forces and which of
+    them have no boundary pair (computed once per test session)."""
+    if "largest" not in _cache:
+        s = W.lattice_box(n=W.APOA1_N * 16)
+        sel = np.random.default_rng(3).choice(s.n, size=2048, replace=False).astype(np.int32)
+        ff = oracle.ForceField.from_system(s)
+        p = s.pos.astype(np.float64)
+        Fo, cond, _ = oracle.forces_atoms(p, s.q, s.type, s.box, ff, sel)
+        _cache["largest"] = (s, sel, Fo, cond, ~_boundary_atoms(p, s.box, s.rc, sel))
+    return _cache["largest"]
+
+
+@pytest.mark.parametrize("mode", ["f32", "fixed64"])
+def test_largest_sweep_size_sampled(cuda_lib, mode):
+    """1,475,584 atoms, the largest point of the size sweep, in the launch the force
+    call makes: 2,048 sampled atoms against the oracle; in FIXED64 Newton's third law
+    holds exactly over the whole system."""
+    api = cuda_lib
+    s, sel, Fo, cond, use = _largest_reference()
+    m = api.ACCUM_F32 if mode == "f32" else api.ACCUM_FIXED64
+    eng = run_forces(api, s, m, algo=0, energy=False)
+    assert int(eng.status.item()) == 0
+    if m == api.ACCUM_FIXED64:
+        assert np.all(eng.forces.cpu().numpy().sum(axis=0, dtype=np.int64) == 0)
+    F = api.forces_to_f64(eng.forces, m).cpu().numpy()
+    assert use.sum() > 1800
+    err = np.linalg.norm(F[sel] - Fo, axis=1)[use] / cond[use]
+    assert err.max() <= TOL_F32, err.max()
