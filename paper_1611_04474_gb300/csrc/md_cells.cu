@@ -39,7 +39,11 @@ k_cell_index(const float4 *__restrict__ pos_q, int n, BoxF box, int *__restrict_
         cell_id[i] = c;
     }
     if (SMEM) {
-        if (c >= 0) atomicAdd(&s_hist[c], 1);
+        // one shared atomic per distinct cell of the warp (consecutive atoms often share
+        // a cell)
+        const unsigned act = __ballot_sync(0xffffffffu, c >= 0);
+        const unsigned grp = __match_any_sync(0xffffffffu, c) & act;
+        if (c >= 0 && (threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&s_hist[c], __popc(grp));
         __syncthreads();
         for (int t = threadIdx.x; t < ncell; t += blockDim.x)
             if (s_hist[t]) atomicAdd(&cell_cnt[t], s_hist[t]);
@@ -193,7 +197,11 @@ k_kick_drift_index(double *__restrict__ pos, double *__restrict__ vel, const voi
         cell_id[i] = c;
     }
     if (SMEM) {
-        if (c >= 0) atomicAdd(&s_hist[c], 1);
+        // one shared atomic per distinct cell of the warp (consecutive atoms often share
+        // a cell)
+        const unsigned act = __ballot_sync(0xffffffffu, c >= 0);
+        const unsigned grp = __match_any_sync(0xffffffffu, c) & act;
+        if (c >= 0 && (threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&s_hist[c], __popc(grp));
         __syncthreads();
         for (int t = threadIdx.x; t < ncell; t += blockDim.x)
             if (s_hist[t]) atomicAdd(&cell_cnt[t], s_hist[t]);
