@@ -240,6 +240,17 @@ def combine_ranks(pairs: float, step_ms: float, e2e_ms: float, device=None):
     return float(p[0]), float(t[0]), float(t[1])
 
 
+def bench_config(s, args, world: int) -> dict:
+    """The workload description both arms print (the same config for the same run)."""
+    return {"workload": f"lattice_{s.n}_apoa1_box", "atoms": s.n, "box": [float(x) for x in s.box],
+            "rc": s.rc, "cells": [int(v) for v in np.floor(s.box / s.rc)],
+            "step": "velocity-Verlet MD step (rebuild+forces+VV)",
+            "force_field": "8 LJ types, sigma x0.5 (1.25-1.9 A), masses 12-16 amu, q~N(0,0.4)",
+            "accum": args.mode, "algo": args.algo, "dt_fs": args.dt,
+            "l2": "flushed (256 MB write) before every timed step",
+            "parallelism": f"replicas x{world}"}
+
+
 def cpu_oracle_rate(s, seconds: float, seed: int = 0, gpu_forces=None):
     """The FP64 oracle as it stands, single-threaded, on a sample of the workload's atoms:
     forces on sampled atoms over the full cell list.  Returns (pairs/s, sample text,
@@ -300,8 +311,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"lattice_{s.n}_apoa1_box", "atoms": s.n, "rc": s.rc,
-                       "box": [float(x) for x in s.box]},
+            "config": bench_config(s, args, world),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -433,12 +443,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": t_step / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if mode == api.ACCUM_F32 else "f32+int64",
         "data": "synthetic",
-        "config": {"workload": f"lattice_{s.n}_apoa1_box", "atoms": s.n, "box": [float(x) for x in s.box],
-                   "rc": s.rc, "cells": eng.dims, "step": "velocity-Verlet MD step (rebuild+forces+VV)",
-                   "force_field": "8 LJ types, sigma x0.5 (1.25-1.9 A), masses 12-16 amu, q~N(0,0.4)",
-                   "accum": args.mode, "algo": args.algo, "dt_fs": args.dt,
-                   "l2": "flushed (256 MB write) before every timed step",
-                   "parallelism": f"replicas x{world}"},
+        "config": bench_config(s, args, world),
         "md_steps_per_s": 1e3 * args.steps / t_step,
         "pairs_per_step": pairs_per_step,
         "candidates_per_eval": candidates,
