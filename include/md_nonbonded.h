@@ -73,9 +73,9 @@ extern "C" {
 #define MD_ALGO_DEFAULT 0
 #define MD_ALGO_FULL_SHELL 1 /* one thread per home atom over all 27 neighbour cells (Alg. 1) */
 #define MD_ALGO_HALF_SHELL 2 /* each cell pair once, reactions by Newton's third law */
-#define MD_ALGO_CLUSTER 3    /* the half shell filtered by clusters of 4 x 8 atoms, every pair of
-                                a cluster pair in range evaluated; boxes with an axis of 2
-                                cells run MD_ALGO_HALF_SHELL */
+#define MD_ALGO_CLUSTER 3    /* the half shell filtered by clusters of 8 atoms, every pair of
+                                a cluster pair in range evaluated (per-pair minimum image in
+                                boxes with an axis of 2 cells) */
 
 /* Force-field constants of Eq. 1-2.  Host struct; AB is a DEVICE pointer to
  * float[ntypes][ntypes][2] holding (A_ij, B_ij) of Eq. 1 (symmetric in i,j). */
@@ -249,8 +249,7 @@ int md_batch_step(int32_t nsys, const md_system_desc *systems, double *pos, doub
 /*
  * Kernel shapes of the batched force launches.  A shape is a performance choice only:
  * every shape finds the same pairs, and in MD_ACCUM_FIXED64 gives the same bits.
- *   0  default: the cluster-pair kernel (MD_ALGO_CLUSTER) for systems with >= 3 cells
- *      on every axis; shape 1 for systems with an axis of 2 cells
+ *   0  default: the cluster-pair kernel (MD_ALGO_CLUSTER)
  *   1  half-shell kernel, 4 warps per block, 256 (F32) or 128 (FIXED64) buffered pairs
  *      per warp
  *   2  half-shell kernel, 2 warps per block, 256 buffered pairs per warp

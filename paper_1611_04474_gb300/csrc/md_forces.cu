@@ -210,7 +210,6 @@ cudaError_t launch_forces(const ForceArgs &a, const WsLayout &ws, char *wsp, cud
     int algo = a.algo;
     if (algo == MD_ALGO_DEFAULT || a.mode == MD_ACCUM_F64)
         algo = a.mode == MD_ACCUM_F64 ? MD_ALGO_FULL_SHELL : MD_ALGO_CLUSTER;
-    if (algo == MD_ALGO_CLUSTER && !cluster_kernel_applies(a.box)) algo = MD_ALGO_HALF_SHELL;
     int nblocks = a.box.ncell;
     if (algo == MD_ALGO_CLUSTER) {
         cudaError_t e = launch_cluster(a, ws, wsp, partials, &nblocks, stream);

@@ -182,14 +182,16 @@ struct CluSmem {
 struct CluConst {
     float kc, rc2, rc2m;
     float lo[3];
+    float L[3], Lhi[3], Llo[3], invL[3];  // per-pair minimum image (boxes with a 2-cell axis)
     int T;
     uint32_t *status;
 };
 
 // Home cluster ic against every neighbour cluster of the staged tile in range.
 // DIAG: the neighbour tile is the home tile (pairs ia < ja only); SHIFT: the cell
-// pair has a remainder shift to add to the difference.
-template <int MODE, int STATS, bool DIAG, bool SHIFT>
+// pair has a remainder shift to add to the difference; MI: the per-pair minimum image
+// (boxes with an axis of 2 cells, unshifted tiles).
+template <int MODE, int STATS, bool DIAG, bool SHIFT, bool MI>
 __device__ __forceinline__ void cluster_row(CluSmem<MODE> &sm, const float2 *s_ab,
                                             const CluConst &k, int ic, int njc, int mh, int warp,
                                             int lane, float &e_lj, float &e_c, float &vir,
@@ -210,6 +212,16 @@ __device__ __forceinline__ void cluster_row(CluSmem<MODE> &sm, const float2 *s_a
     float ib[6];
 #pragma unroll
     for (int d = 0; d < 6; ++d) ib[d] = sm.ib[d][ic];
+    // MI: the box filter takes the gap between the clusters' nearest images, from their
+    // centres and half extents (widened by a few ulps of L for the roundings)
+    float ic_c[3], ic_e[3];
+    if (MI) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            ic_c[d] = 0.5f * (ib[d] + ib[d + 3]);
+            ic_e[d] = 0.5f * (ib[d + 3] - ib[d]) + 4.0f * 1.1920929e-7f * k.L[d];
+        }
+    }
     // home-atom sums: F32 packed (atom ia0 low, ia1 high); FIXED64 one integer each
     f2 ax2 = 0ull, ay2 = 0ull, az2 = 0ull;
     Acc ax0 = Acc(0), ay0 = Acc(0), az0 = Acc(0), ax1 = Acc(0), ay1 = Acc(0), az1 = Acc(0);
@@ -219,10 +231,24 @@ __device__ __forceinline__ void cluster_row(CluSmem<MODE> &sm, const float2 *s_a
         const int jt = jb + lane;
         bool in = false;
         if (jt < njc) {
-            const float gx = fmaxf(0.f, fmaxf(ib[0] - sm.jb[3][jt], sm.jb[0][jt] - ib[3]));
-            const float gy = fmaxf(0.f, fmaxf(ib[1] - sm.jb[4][jt], sm.jb[1][jt] - ib[4]));
-            const float gz = fmaxf(0.f, fmaxf(ib[2] - sm.jb[5][jt], sm.jb[2][jt] - ib[5]));
-            in = gx * gx + gy * gy + gz * gz < k.rc2m;
+            if (MI) {
+                float g2 = 0.f;
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    const float jcen = 0.5f * (sm.jb[d][jt] + sm.jb[d + 3][jt]);
+                    const float jext = 0.5f * (sm.jb[d + 3][jt] - sm.jb[d][jt]);
+                    float dd = ic_c[d] - jcen;
+                    dd -= k.L[d] * rintf(dd * k.invL[d]);
+                    const float gap = fmaxf(0.f, fabsf(dd) - ic_e[d] - jext);
+                    g2 += gap * gap;
+                }
+                in = g2 < k.rc2m;
+            } else {
+                const float gx = fmaxf(0.f, fmaxf(ib[0] - sm.jb[3][jt], sm.jb[0][jt] - ib[3]));
+                const float gy = fmaxf(0.f, fmaxf(ib[1] - sm.jb[4][jt], sm.jb[1][jt] - ib[4]));
+                const float gz = fmaxf(0.f, fmaxf(ib[2] - sm.jb[5][jt], sm.jb[2][jt] - ib[5]));
+                in = gx * gx + gy * gy + gz * gz < k.rc2m;
+            }
         }
         unsigned todo = __ballot_sync(0xffffffffu, in);
         while (todo) {
@@ -234,11 +260,24 @@ __device__ __forceinline__ void cluster_row(CluSmem<MODE> &sm, const float2 *s_a
             const float2 ab0 = s_ab[t0 + tj], ab1 = s_ab[t1 + tj];  // (A, -B)
             // pair_r2 and pair_f element by element in packed FP32x2 instructions
             // (each rounds as its scalar counterpart)
-            f2 dx = f2_sub(xi, f2_dup(pj.x)), dy = f2_sub(yi, f2_dup(pj.y)), dz = f2_sub(zi, f2_dup(pj.z));
-            if (SHIFT) {
-                dx = f2_add(dx, lox);
-                dy = f2_add(dy, loy);
-                dz = f2_add(dz, loz);
+            f2 dx, dy, dz;
+            if (MI) {
+                // the library's per-pair minimum image, element by element
+                dx = f2_make(min_image_f32(p0.x, pj.x, k.Lhi[0], k.Llo[0], k.invL[0]),
+                             min_image_f32(p1.x, pj.x, k.Lhi[0], k.Llo[0], k.invL[0]));
+                dy = f2_make(min_image_f32(p0.y, pj.y, k.Lhi[1], k.Llo[1], k.invL[1]),
+                             min_image_f32(p1.y, pj.y, k.Lhi[1], k.Llo[1], k.invL[1]));
+                dz = f2_make(min_image_f32(p0.z, pj.z, k.Lhi[2], k.Llo[2], k.invL[2]),
+                             min_image_f32(p1.z, pj.z, k.Lhi[2], k.Llo[2], k.invL[2]));
+            } else {
+                dx = f2_sub(xi, f2_dup(pj.x));
+                dy = f2_sub(yi, f2_dup(pj.y));
+                dz = f2_sub(zi, f2_dup(pj.z));
+                if (SHIFT) {
+                    dx = f2_add(dx, lox);
+                    dy = f2_add(dy, loy);
+                    dz = f2_add(dz, loz);
+                }
             }
             const f2 r2 = f2_fma(dz, dz, f2_fma(dy, dy, f2_mul(dx, dx)));
             float r20, r21;
@@ -373,7 +412,7 @@ __device__ __forceinline__ void cluster_row(CluSmem<MODE> &sm, const float2 *s_a
     }
 }
 
-template <int MODE, int STATS, bool BATCHED>
+template <int MODE, int STATS, bool BATCHED, bool MI>
 __global__ void __launch_bounds__(kCT, MODE == MD_ACCUM_FIXED64 ? 6 : 7)
 k_cluster(CluArgs a, BatchArgs bt, unsigned long long *sys_pair_count)
 {
@@ -394,10 +433,20 @@ k_cluster(CluArgs a, BatchArgs bt, unsigned long long *sys_pair_count)
     bool valid;
     int sid = 0;
     if (BATCHED) {
-        const int cell = bt.cell_list[blockIdx.x];  // systems with >= 3 cells per axis
+        // regular systems' cells first in cell_list, then those with a 2-cell axis
+        const int cell = bt.cell_list[(MI ? bt.ncell_reg : 0) + blockIdx.x];
         sid = bt.cell_sys[cell];
         const SysDesc &d = bt.sys[sid];
         valid = cell_pair(d.box, cell - d.cell_offset, blockIdx.y, g);
+        if (MI) {
+#pragma unroll
+            for (int e = 0; e < 3; ++e) {
+                k.L[e] = (float)d.box.L[e];
+                k.Lhi[e] = d.box.Lhi[e];
+                k.Llo[e] = d.box.Llo[e];
+                k.invL[e] = d.box.invL[e];
+            }
+        }
         g.home += d.cell_offset;
         g.nbr += d.cell_offset;
         k.T = d.ntypes;
@@ -407,6 +456,15 @@ k_cluster(CluArgs a, BatchArgs bt, unsigned long long *sys_pair_count)
         k.rc2m = d.rc2m;
     } else {
         valid = cell_pair(a.box, blockIdx.x, blockIdx.y, g);
+        if (MI) {
+#pragma unroll
+            for (int e = 0; e < 3; ++e) {
+                k.L[e] = (float)a.box.L[e];
+                k.Lhi[e] = a.box.Lhi[e];
+                k.Llo[e] = a.box.Llo[e];
+                k.invL[e] = a.box.invL[e];
+            }
+        }
         k.T = a.ntypes;
         AB = a.AB;
         k.kc = a.kc;
@@ -489,11 +547,11 @@ k_cluster(CluArgs a, BatchArgs bt, unsigned long long *sys_pair_count)
             // home clusters handed out one at a time, so that warps finish together
             for (int ic = warp; ic < nic;) {
                 if (diag)
-                    cluster_row<MODE, STATS, true, false>(sm, s_ab, k, ic, njc, mh, warp, lane, e_lj, e_c, vir, cnt);
-                else if (shift)
-                    cluster_row<MODE, STATS, false, true>(sm, s_ab, k, ic, njc, mh, warp, lane, e_lj, e_c, vir, cnt);
+                    cluster_row<MODE, STATS, true, false, MI>(sm, s_ab, k, ic, njc, mh, warp, lane, e_lj, e_c, vir, cnt);
+                else if (!MI && shift)
+                    cluster_row<MODE, STATS, false, true, false>(sm, s_ab, k, ic, njc, mh, warp, lane, e_lj, e_c, vir, cnt);
                 else
-                    cluster_row<MODE, STATS, false, false>(sm, s_ab, k, ic, njc, mh, warp, lane, e_lj, e_c, vir, cnt);
+                    cluster_row<MODE, STATS, false, false, MI>(sm, s_ab, k, ic, njc, mh, warp, lane, e_lj, e_c, vir, cnt);
                 int nx = 0;
                 if (lane == 0) nx = atomicAdd(&sm.next, 1);
                 ic = __shfl_sync(0xffffffffu, nx, 0);
@@ -588,24 +646,27 @@ k_finalize_clu(const void *__restrict__ accum, const int32_t *__restrict__ corde
     }
 }
 
-template <int MODE, int STATS, bool BATCHED = false>
+template <int MODE, int STATS, bool BATCHED = false, bool MI = false>
 void launch_cluster_t(const CluArgs &c, dim3 grid, cudaStream_t stream, const BatchArgs &b = BatchArgs{},
                       unsigned long long *sys_pair_count = nullptr)
 {
     const size_t dyn = sizeof(float2) * (size_t)c.ntypes * (size_t)c.ntypes;
     static const cudaError_t attr = cudaFuncSetAttribute(
-        k_cluster<MODE, STATS, BATCHED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        k_cluster<MODE, STATS, BATCHED, MI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
         (int)(sizeof(float2) * kMaxTypes * kMaxTypes));
     (void)attr;
-    k_cluster<MODE, STATS, BATCHED><<<grid, kCT, dyn, stream>>>(c, b, sys_pair_count);
+    k_cluster<MODE, STATS, BATCHED, MI><<<grid, kCT, dyn, stream>>>(c, b, sys_pair_count);
+}
+
+template <int MODE, bool MI>
+void launch_cluster_stats(int stats, const CluArgs &c, dim3 grid, cudaStream_t stream)
+{
+    if (stats == kStatsEnergy) launch_cluster_t<MODE, kStatsEnergy, false, MI>(c, grid, stream);
+    else if (stats == kStatsCount) launch_cluster_t<MODE, kStatsCount, false, MI>(c, grid, stream);
+    else launch_cluster_t<MODE, kStatsNone, false, MI>(c, grid, stream);
 }
 
 }  // namespace
-
-bool cluster_kernel_applies(const BoxF &box)
-{
-    return half_shell_pairs_per_cell(box) == 14;
-}
 
 cudaError_t launch_cluster(const ForceArgs &a, const WsLayout &ws, char *wsp, Partial *partials,
                            int *nblocks_out, cudaStream_t stream)
@@ -628,34 +689,36 @@ cudaError_t launch_cluster(const ForceArgs &a, const WsLayout &ws, char *wsp, Pa
     c.AB = a.AB;
     c.ntypes = a.ntypes;
     c.kc = a.k_coulomb;
-    cutoff_thresholds(a.box, a.rc64, false, &c.rc2, &c.rc2m);
+    const int per_cell = half_shell_pairs_per_cell(a.box);
+    const bool mi = per_cell == 27;  // an axis of 2 cells: per-pair minimum image
+    cutoff_thresholds(a.box, a.rc64, mi, &c.rc2, &c.rc2m);
     c.accum = accum;
     c.n = a.n;
     c.partials = partials;
     c.status = a.status;
-    dim3 grid(a.box.ncell, 14);
+    dim3 grid(a.box.ncell, per_cell);
     const int stats = a.energy_virial_out ? kStatsEnergy : (a.pair_count_out ? kStatsCount : kStatsNone);
     if (a.mode == MD_ACCUM_FIXED64) {
-        if (stats == kStatsEnergy) launch_cluster_t<MD_ACCUM_FIXED64, kStatsEnergy>(c, grid, stream);
-        else if (stats == kStatsCount) launch_cluster_t<MD_ACCUM_FIXED64, kStatsCount>(c, grid, stream);
-        else launch_cluster_t<MD_ACCUM_FIXED64, kStatsNone>(c, grid, stream);
+        if (mi) launch_cluster_stats<MD_ACCUM_FIXED64, true>(stats, c, grid, stream);
+        else launch_cluster_stats<MD_ACCUM_FIXED64, false>(stats, c, grid, stream);
     } else {
-        if (stats == kStatsEnergy) launch_cluster_t<MD_ACCUM_F32, kStatsEnergy>(c, grid, stream);
-        else if (stats == kStatsCount) launch_cluster_t<MD_ACCUM_F32, kStatsCount>(c, grid, stream);
-        else launch_cluster_t<MD_ACCUM_F32, kStatsNone>(c, grid, stream);
+        if (mi) launch_cluster_stats<MD_ACCUM_F32, true>(stats, c, grid, stream);
+        else launch_cluster_stats<MD_ACCUM_F32, false>(stats, c, grid, stream);
     }
-    *nblocks_out = a.box.ncell * 14;
+    *nblocks_out = a.box.ncell * per_cell;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return launch_finalize_cluster(a, accum, ws, wsp, a.n, stream);
 }
 
-// Batched cluster kernel over the regular systems' cells (b.cell_list[0 .. ncell_reg)).
-cudaError_t launch_cluster_batched(int mode, const BatchArgs &b, const int32_t *cell_start,
+// Batched cluster kernel over the regular systems' cells (b.cell_list[0 .. ncell_reg),
+// 14 cell pairs each) or, mi, over those of the systems with a 2-cell axis (27 each).
+cudaError_t launch_cluster_batched(int mode, bool mi, const BatchArgs &b, const int32_t *cell_start,
                                    const float4 *pq, const int32_t *ty, void *accum,
                                    Partial *partials, uint32_t *status,
                                    unsigned long long *sys_pair_count, cudaStream_t stream)
 {
-    if (b.ncell_reg <= 0) return cudaSuccess;
+    const int ncells = mi ? b.ncell_mi : b.ncell_reg;
+    if (ncells <= 0) return cudaSuccess;
     CluArgs c = {};
     c.cell_start = cell_start;
     c.pq = pq;  // cluster-ordered tiles
@@ -665,13 +728,24 @@ cudaError_t launch_cluster_batched(int mode, const BatchArgs &b, const int32_t *
     c.n = b.n;
     c.partials = partials;
     c.status = status;
-    dim3 grid(b.ncell_reg, 14);
+    dim3 grid(ncells, mi ? 27 : 14);
+    const bool cnt = sys_pair_count != nullptr;
     if (mode == MD_ACCUM_FIXED64) {
-        if (sys_pair_count) launch_cluster_t<MD_ACCUM_FIXED64, kStatsCount, true>(c, grid, stream, b, sys_pair_count);
-        else launch_cluster_t<MD_ACCUM_FIXED64, kStatsNone, true>(c, grid, stream, b, nullptr);
+        if (mi) {
+            if (cnt) launch_cluster_t<MD_ACCUM_FIXED64, kStatsCount, true, true>(c, grid, stream, b, sys_pair_count);
+            else launch_cluster_t<MD_ACCUM_FIXED64, kStatsNone, true, true>(c, grid, stream, b, nullptr);
+        } else {
+            if (cnt) launch_cluster_t<MD_ACCUM_FIXED64, kStatsCount, true, false>(c, grid, stream, b, sys_pair_count);
+            else launch_cluster_t<MD_ACCUM_FIXED64, kStatsNone, true, false>(c, grid, stream, b, nullptr);
+        }
     } else {
-        if (sys_pair_count) launch_cluster_t<MD_ACCUM_F32, kStatsCount, true>(c, grid, stream, b, sys_pair_count);
-        else launch_cluster_t<MD_ACCUM_F32, kStatsNone, true>(c, grid, stream, b, nullptr);
+        if (mi) {
+            if (cnt) launch_cluster_t<MD_ACCUM_F32, kStatsCount, true, true>(c, grid, stream, b, sys_pair_count);
+            else launch_cluster_t<MD_ACCUM_F32, kStatsNone, true, true>(c, grid, stream, b, nullptr);
+        } else {
+            if (cnt) launch_cluster_t<MD_ACCUM_F32, kStatsCount, true, false>(c, grid, stream, b, sys_pair_count);
+            else launch_cluster_t<MD_ACCUM_F32, kStatsNone, true, false>(c, grid, stream, b, nullptr);
+        }
     }
     return cudaGetLastError();
 }

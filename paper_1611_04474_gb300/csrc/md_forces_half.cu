@@ -532,7 +532,7 @@ void launch_half_t(const HalfArgs &h, dim3 grid, cudaStream_t stream, const Batc
 
 // The half-shell shapes of the batched launches (md_batch_tuning): {warps per CTA,
 // survivors buffered per warp} = 1 {4, default}, 2 {2, 256}, 3 {8, 256}, 4 {4, 128}.
-// Shape 0 is the cluster kernel for regular cells and shape 1 for 2-cell boxes.
+// Shape 0 is the cluster kernel.
 static_assert(MD_BATCH_SHAPES == 5, "one case per shape");
 
 template <int MODE, bool MI>
@@ -592,8 +592,8 @@ cudaError_t launch_forces_batched(const ForceArgs &a, const BatchArgs &b,
         h.partials = partials;
         dim3 grid(b.ncell_reg, 14);
         if (shape_reg == 0)
-            e = launch_cluster_batched(a.mode, b, a.cell_start, h.pq, h.ty, accum, partials, a.status,
-                                       sys_pair_count, stream);
+            e = launch_cluster_batched(a.mode, false, b, a.cell_start, h.pq, h.ty, accum, partials,
+                                       a.status, sys_pair_count, stream);
         else if (a.mode == MD_ACCUM_FIXED64) launch_batched_shape<MD_ACCUM_FIXED64, false>(shape_reg, h, grid, stream, b, sys_pair_count);
         else launch_batched_shape<MD_ACCUM_F32, false>(shape_reg, h, grid, stream, b, sys_pair_count);
         if (e != cudaSuccess) return e;
@@ -601,8 +601,12 @@ cudaError_t launch_forces_batched(const ForceArgs &a, const BatchArgs &b,
     if (b.ncell_mi > 0) {
         h.partials = partials + (size_t)14 * b.ncell_reg;
         dim3 grid(b.ncell_mi, 27);
-        if (a.mode == MD_ACCUM_FIXED64) launch_batched_shape<MD_ACCUM_FIXED64, true>(shape_mi, h, grid, stream, b, sys_pair_count);
+        if (shape_mi == 0)
+            e = launch_cluster_batched(a.mode, true, b, a.cell_start, h.pq, h.ty, accum, h.partials,
+                                       a.status, sys_pair_count, stream);
+        else if (a.mode == MD_ACCUM_FIXED64) launch_batched_shape<MD_ACCUM_FIXED64, true>(shape_mi, h, grid, stream, b, sys_pair_count);
         else launch_batched_shape<MD_ACCUM_F32, true>(shape_mi, h, grid, stream, b, sys_pair_count);
+        if (e != cudaSuccess) return e;
     }
     if ((e = launch_finalize_cluster(a, accum, ws, wsp, b.n, stream)) != cudaSuccess) return e;
     return cudaGetLastError();

@@ -190,11 +190,11 @@ __device__ __forceinline__ void load_force(const void *forces, int mode, int i, 
 // remainder Llo is applied last.
 __device__ __forceinline__ float min_image_f32(float xi, float xj, float Lhi, float Llo, float invL)
 {
-    float d0 = xi - xj;
-    float k = rintf(d0 * invL);
-    float a = xi - (k > 0.0f ? Lhi : 0.0f);
-    float b = xj - (k < 0.0f ? Lhi : 0.0f);
-    return (a - b) - k * Llo;
+    const float d0 = __fsub_rn(xi, xj);
+    const float k = rintf(__fmul_rn(d0, invL));
+    const float a = __fsub_rn(xi, k > 0.0f ? Lhi : 0.0f);
+    const float b = __fsub_rn(xj, k < 0.0f ? Lhi : 0.0f);
+    return __fsub_rn(__fsub_rn(a, b), __fmul_rn(k, Llo));
 }
 
 __device__ __forceinline__ double min_image_f64(double xi, double xj, double L)
@@ -341,7 +341,6 @@ int half_shell_pairs_per_cell(const BoxF &box);
 void cutoff_thresholds(const BoxF &box, double rc, bool mi, float *rc2, float *rc2m);
 cudaError_t launch_half_shell(const ForceArgs &a, const WsLayout &ws, char *wsp, Partial *partials,
                               int *nblocks_out, cudaStream_t stream);
-bool cluster_kernel_applies(const BoxF &box);
 cudaError_t launch_finalize_cluster(const ForceArgs &a, const void *accum, const WsLayout &ws,
                                     char *wsp, int n, cudaStream_t stream);
 cudaError_t launch_cluster(const ForceArgs &a, const WsLayout &ws, char *wsp, Partial *partials,
@@ -356,7 +355,7 @@ struct BatchArgs {
     int nsys, n, ncell, ncell_mi, ncell_reg;
     int max_ntypes;  // largest LJ table of the batch: sizes the kernels' shared copy
 };
-cudaError_t launch_cluster_batched(int mode, const BatchArgs &b, const int32_t *cell_start,
+cudaError_t launch_cluster_batched(int mode, bool mi, const BatchArgs &b, const int32_t *cell_start,
                                    const float4 *pq, const int32_t *ty, void *accum,
                                    Partial *partials, uint32_t *status,
                                    unsigned long long *sys_pair_count, cudaStream_t stream);
