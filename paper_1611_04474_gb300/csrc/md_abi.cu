@@ -102,7 +102,7 @@ WsLayout ws_layout(int n, int ncell)
     WsLayout w;
     size_t nn = (size_t)(n > 0 ? n : 1);
     size_t nc = (size_t)(ncell > 0 ? ncell : 1);
-    int slots = 27 * ncell;  // one partial per CTA of the half-shell kernel at most
+    int slots = 27 * ncell;  // one partial per CTA of a cell-pair kernel at most
     int kin = (int)((nn + 255) / 256);
     if (slots < kin) slots = kin;
     if (slots < 2048) slots = 2048;

@@ -29,7 +29,9 @@
 //            its 4 lanes by two shuffles, and added to a warp-private shared array
 //            (F32) or with one integer shared atomic per component (FIXED64).
 //
-// Boxes with an axis of 2 cells use the half-shell kernel.
+// Boxes with an axis of 2 cells meet each distinct stencil cell once, with unshifted
+// tiles: the filter takes the gap between the clusters' nearest images and each pair
+// the per-pair minimum image.
 #include <math.h>
 
 #include "md_internal.cuh"
