@@ -14,6 +14,8 @@ namespace mdnb {
 namespace {
 
 constexpr int kIndexThreads = 1024;  // atoms per block of the counting passes
+constexpr int kStepThreads = 256;    // atoms per block of the fused MD-step pass (FP64 work)
+constexpr int kStepSmemCells = 4 * kStepThreads;  // per-block shared histogram up to this
 constexpr int kSmemCells = 8192;     // per-block shared histogram up to this many cells
 constexpr int kScanThreads = 1024;
 constexpr int kSortThreads = 128;
@@ -148,7 +150,7 @@ k_cell_sort(const int *__restrict__ cell_start, const int *__restrict__ perm_tmp
 // work of k_kick, k_drift_wrap and k_cell_index in one pass.  BATCHED: each atom's box
 // from its system, cells numbered over the batch.
 template <bool SMEM, bool BATCHED>
-__global__ void __launch_bounds__(kIndexThreads)
+__global__ void __launch_bounds__(kStepThreads)
 k_kick_drift_index(double *__restrict__ pos, double *__restrict__ vel, const void *__restrict__ forces,
                    int mode, const float *__restrict__ inv_mass, const float *__restrict__ q, int n,
                    BoxF box_in, BatchArgs b, double dt, double half_dt, int kick,
@@ -328,15 +330,15 @@ cudaError_t launch_kick_drift_build(double *pos, double *vel, const void *forces
     cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)ncell, stream);
     if (e != cudaSuccess) return e;
     if (n > 0) {
-        const int g = (n + kIndexThreads - 1) / kIndexThreads;
-        const size_t sm = ncell <= kSmemCells ? sizeof(int) * (size_t)ncell : 0;
+        const int g = (n + kStepThreads - 1) / kStepThreads;
+        const size_t sm = ncell <= kStepSmemCells ? sizeof(int) * (size_t)ncell : 0;
         const int k = kick ? 1 : 0;
         if (b) {
-            if (sm) k_kick_drift_index<true, true><<<g, kIndexThreads, sm, stream>>>(pos, vel, forces, mode, inv_mass, q, n, box_in, bb, dt, half_dt, k, pos_q, cell_id, cnt, status);
-            else k_kick_drift_index<false, true><<<g, kIndexThreads, 0, stream>>>(pos, vel, forces, mode, inv_mass, q, n, box_in, bb, dt, half_dt, k, pos_q, cell_id, cnt, status);
+            if (sm) k_kick_drift_index<true, true><<<g, kStepThreads, sm, stream>>>(pos, vel, forces, mode, inv_mass, q, n, box_in, bb, dt, half_dt, k, pos_q, cell_id, cnt, status);
+            else k_kick_drift_index<false, true><<<g, kStepThreads, 0, stream>>>(pos, vel, forces, mode, inv_mass, q, n, box_in, bb, dt, half_dt, k, pos_q, cell_id, cnt, status);
         } else {
-            if (sm) k_kick_drift_index<true, false><<<g, kIndexThreads, sm, stream>>>(pos, vel, forces, mode, inv_mass, q, n, box_in, bb, dt, half_dt, k, pos_q, cell_id, cnt, status);
-            else k_kick_drift_index<false, false><<<g, kIndexThreads, 0, stream>>>(pos, vel, forces, mode, inv_mass, q, n, box_in, bb, dt, half_dt, k, pos_q, cell_id, cnt, status);
+            if (sm) k_kick_drift_index<true, false><<<g, kStepThreads, sm, stream>>>(pos, vel, forces, mode, inv_mass, q, n, box_in, bb, dt, half_dt, k, pos_q, cell_id, cnt, status);
+            else k_kick_drift_index<false, false><<<g, kStepThreads, 0, stream>>>(pos, vel, forces, mode, inv_mass, q, n, box_in, bb, dt, half_dt, k, pos_q, cell_id, cnt, status);
         }
     }
     k_scan_cells<<<1, kScanThreads, 0, stream>>>(cnt, ncell, cell_start);
