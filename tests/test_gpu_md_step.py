@@ -132,3 +132,42 @@ def test_nve_energy_is_conserved_on_the_gentle_system(cuda_lib):
     # the three modes integrate the same dynamics
     assert abs(drifts[api.ACCUM_F32] - drifts[api.ACCUM_F64]) < 0.05, drifts
     assert abs(drifts[api.ACCUM_FIXED64] - drifts[api.ACCUM_F64]) < 0.05, drifts
+
+
+def test_step_cells_of_every_size(cuda_lib):
+    """The MD step builds its cells straight in cluster order, with a separate path for
+    cells of more than 1,024 atoms. On a box that holds one such cell (1,331 atoms) and
+    cells of a few dozen, the start forces of md_step are the bits of md_nonbonded_forces
+    in FIXED64, and after one FIXED64 step the forces match the oracle at the new
+    positions."""
+    from tests.test_gpu_parity import _custom
+
+    api = cuda_lib
+    rng = np.random.default_rng(11)
+    b = np.stack(np.meshgrid(*[np.arange(11)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    blob = 0.2 + 0.33 * b + rng.uniform(-0.02, 0.02, b.shape)
+    rest = rng.uniform((5.5, 0.0, 0.0), (12.0, 12.0, 12.0), (300, 3))
+    keep = np.ones(len(rest), bool)
+    for k in range(len(rest)):
+        d = np.linalg.norm(rest[:k][keep[:k]] - rest[k], axis=1)
+        keep[k] = not np.any(d < 0.8)
+    s = _custom(np.concatenate([blob, rest[keep]]), (12.0, 12.0, 12.0), rc=4.0)
+    ref = api.Engine(s, mode=api.ACCUM_FIXED64)
+    ref.build_cells()
+    ref.compute_forces()
+    eng = api.Engine(s, mode=api.ACCUM_FIXED64)
+    eng.step(0, dt_fs=0.001)
+    torch.cuda.synchronize()
+    assert int(eng.status.item()) == 0
+    assert np.array_equal(eng.forces.cpu().numpy(), ref.forces.cpu().numpy())
+    eng.step(1, dt_fs=0.001)
+    torch.cuda.synchronize()
+    p = eng.pos.cpu().numpy().astype(np.float32).astype(np.float64)
+    s1 = W.System(s.name, p.astype(np.float32), s.q, s.type, s.box, s.rc, s.sigma, s.eps, s.AB,
+                  s.mass, s.vel)
+    ff = oracle.ForceField.from_system(s1)
+    r = oracle.forces_cells(p, s1.q, s1.type, s1.box, ff)
+    alts, nb = boundary_alternatives(p, s1, ff, r.F)
+    F = api.forces_to_f64(eng.forces, api.ACCUM_FIXED64).cpu().numpy()
+    err = force_errors(F, r.F, r.cond, alts)
+    assert err["max_norm"] <= 1e-5, err
