@@ -18,12 +18,14 @@
 //   force:   a warp evaluates the 8 x 8 pairs of one cluster pair: lane i + 4 j holds
 //            home atoms i and i + 4 and neighbour atom j and evaluates those two pairs,
 //            with packed FP32x2 instructions (Blackwell's paired FP32 ALU) and the
-//            exact test r^2 < rc^2 per pair.  The packed chain is pair_r2 / pair_f
-//            element by element on the same staged coordinates and shifts as the
-//            half-shell kernel, and every packed instruction rounds as its scalar
-//            counterpart, so MD_ACCUM_FIXED64 integers are the same bits as the other
+//            exact test r^2 < rc^2 per pair.  In MD_ACCUM_FIXED64 the packed chain is
+//            pair_r2 / pair_f element by element on the same staged coordinates and
+//            shifts as the half-shell kernel, and every packed instruction rounds as
+//            its scalar counterpart, so its integers are the same bits as the other
 //            kernels'.  (pair_f ends in a fused multiply-add: a separate multiply
 //            feeding an add was fused by the compiler in the packed chain only.)
+//            MD_ACCUM_F32 takes k q_i once per home cluster and 1/r from the
+//            hardware rsqrt without pair_f's Newton step.
 //   reduce:  home-atom forces stay in registers for the whole home cluster; the
 //            reaction on each neighbour atom is summed over its two pairs, then over
 //            its 4 lanes by two shuffles, and added to a warp-private shared array
@@ -296,7 +298,9 @@ __device__ __forceinline__ void cluster_row(CluSmem<MODE> &sm, const float2 *s_a
             asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(r20));
             asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y1) : "f"(r21));
             const f2 y = f2_make(y0, y1);
-            const f2 ir = f2_mul(y, f2_fma(f2_mul(m05, r2), f2_mul(y, y), c15));
+            // FIXED64 refines 1/r with pair_f's Newton step; F32 uses the hardware
+            // approximation as it is (the force error stays at 6e-7 of the term sum)
+            const f2 ir = MODE == MD_ACCUM_FIXED64 ? f2_mul(y, f2_fma(f2_mul(m05, r2), f2_mul(y, y), c15)) : y;
             const f2 ir2 = f2_mul(ir, ir);
             const f2 ir6 = f2_mul(f2_mul(ir2, ir2), ir2);
             const f2 ir8 = f2_mul(ir6, ir2);
