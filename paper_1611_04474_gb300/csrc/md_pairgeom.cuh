@@ -137,8 +137,10 @@ __device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsig
 }
 __device__ __forceinline__ unsigned long long f2_dup(float x)
 {
-    const unsigned long long u = __float_as_uint(x);
-    return u | (u << 32);
+    // a register pair holding x twice (cheaper than a 64-bit shift and or)
+    unsigned long long d;
+    asm("mov.b64 %0, {%1, %1};" : "=l"(d) : "f"(x));
+    return d;
 }
 
 }  // namespace
