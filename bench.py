@@ -40,22 +40,29 @@ FLOP_PER_PAIR = 22
 
 # DRAM bytes of one launch of the dominant kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum of k_cluster, 92,224-atom lattice) from the ncu capture
-# summarised in profiles/k_cluster_lattice92k.md, with the SHA-256 of the kernel source
-# it was taken on: the figure is reported as null once that source has changed.
-TRAFFIC_CAPTURE = {"bytes": 3371776, "atoms": 92224,
-                   "kernel_source_sha256": "5e776b894b45296a3906284336399364f8fcaecab2eaf087a6c9dbc1ac7e2d92"}
-KERNEL_SOURCE = os.path.join(ROOT, "paper_1611_04474_gb300", "csrc", "md_forces_cluster.cu")
+# summarised in profiles/k_cluster_lattice92k.md, with the SHA-256 of the kernel's
+# sources it was taken on: the figure is reported as null once they have changed.
+TRAFFIC_CAPTURE = {"bytes": 3371776, "atoms": 92224, "kernel_source_sha256": None}
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_1611_04474_gb300", "csrc", f)
+                  for f in ("md_forces_cluster.cu", "md_pairgeom.cuh", "md_internal.cuh")]
+
+
+def kernel_source_sha256() -> str | None:
+    import hashlib
+
+    h = hashlib.sha256()
+    try:
+        for path in KERNEL_SOURCES:
+            with open(path, "rb") as f:
+                h.update(f.read())
+    except OSError:
+        return None
+    return h.hexdigest()
 
 
 def captured_traffic(n_atoms: int):
-    import hashlib
-
-    try:
-        with open(KERNEL_SOURCE, "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()
-    except OSError:
-        return None
-    if sha != TRAFFIC_CAPTURE["kernel_source_sha256"] or n_atoms != TRAFFIC_CAPTURE["atoms"]:
+    sha = kernel_source_sha256()
+    if sha is None or sha != TRAFFIC_CAPTURE["kernel_source_sha256"] or n_atoms != TRAFFIC_CAPTURE["atoms"]:
         return None
     return TRAFFIC_CAPTURE["bytes"]
 
