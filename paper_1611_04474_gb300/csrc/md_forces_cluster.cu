@@ -24,8 +24,7 @@
 //            its scalar counterpart, so its integers are the same bits as the other
 //            kernels'.  (pair_f ends in a fused multiply-add: a separate multiply
 //            feeding an add was fused by the compiler in the packed chain only.)
-//            MD_ACCUM_F32 takes k q_i once per home cluster and 1/r from the
-//            hardware rsqrt without pair_f's Newton step.
+//            MD_ACCUM_F32 takes k q_i once per home cluster.
 //   reduce:  home-atom forces stay in registers for the whole home cluster; the
 //            reaction on each neighbour atom is summed over its two pairs, then over
 //            its 4 lanes by two shuffles, and added to a warp-private shared array
@@ -210,7 +209,6 @@ __device__ __forceinline__ void cluster_row(CluSmem<MODE> &sm, const float2 *s_a
     const int t0 = sm.ht[ia0] * k.T, t1 = sm.ht[ia1] * k.T;
     const f2 kc2 = f2_make(k.kc, k.kc);
     const f2 kcq = f2_mul(kc2, qi);  // k q_i (F32 path)
-    const f2 m05 = f2_make(-0.5f, -0.5f), c15 = f2_make(1.5f, 1.5f);
     const f2 lox = f2_make(k.lo[0], k.lo[0]), loy = f2_make(k.lo[1], k.lo[1]),
              loz = f2_make(k.lo[2], k.lo[2]);
     float ib[6];
@@ -295,16 +293,14 @@ __device__ __forceinline__ void cluster_row(CluSmem<MODE> &sm, const float2 *s_a
             const f2 kqq = MODE == MD_ACCUM_FIXED64 ? f2_mul(kc2, f2_mul(qi, f2_dup(pj.w)))
                                                     : f2_mul(kcq, f2_dup(pj.w));
             float y0, y1;
-            asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(r20));
-            asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y1) : "f"(r21));
+            y0 = rsqrt_hw(r20);
+            y1 = rsqrt_hw(r21);
             const f2 y = f2_make(y0, y1);
-            // FIXED64 refines 1/r with pair_f's Newton step; F32 uses the hardware
-            // approximation as it is (the force error stays at 6e-7 of the term sum)
-            const f2 ir = MODE == MD_ACCUM_FIXED64 ? f2_mul(y, f2_fma(f2_mul(m05, r2), f2_mul(y, y), c15)) : y;
+            const f2 ir = y;
             const f2 ir2 = f2_mul(ir, ir);
             const f2 ir6 = f2_mul(f2_mul(ir2, ir2), ir2);
             const f2 ir8 = f2_mul(ir6, ir2);
-            const f2 lj = f2_fma(A2, f2_mul(ir8, ir6), f2_mul(nB2, ir8));
+            const f2 lj = f2_mul(ir8, f2_fma(A2, ir6, nB2));
             float f0, f1;
             f2_split(f2_fma(f2_mul(kqq, ir2), ir, lj), f0, f1);
             f0 = ok0 ? f0 : 0.0f;

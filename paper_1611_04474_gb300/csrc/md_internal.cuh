@@ -210,28 +210,27 @@ __device__ __forceinline__ float pair_r2(float dx, float dy, float dz)
     return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
 }
 
-// 1/sqrt(x) from the hardware approximation (MUFU, ~2^-22 relative) refined by one
-// Newton-Raphson step y' = y (3 - x y^2) / 2, which leaves about one ulp.
-__device__ __forceinline__ float rsqrt_nr(float x)
+// 1/sqrt(x) from the hardware approximation (MUFU; relative error near 2^-22, well
+// inside the 1e-5 force criterion, so no refinement step).
+__device__ __forceinline__ float rsqrt_hw(float x)
 {
     float y;
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    const float h = __fmul_rn(0.5f, x);
-    return __fmul_rn(y, __fmaf_rn(-h, __fmul_rn(y, y), 1.5f));
+    return y;
 }
 
-// Scalar f of F = f * r (Eq. 1: A/r^14 - B/r^8, Eq. 2: k q1 q2 / r^3); also returns
-// 1/r, 1/r^2, 1/r^6 for the energies.  The Coulomb term joins the LJ term in one fused
-// multiply-add, so that no separate multiply feeds an add (which a compiler could fuse
-// in one kernel and not in another).
+// Scalar f of F = f * r (Eq. 1: A/r^14 - B/r^8 = (A r^-6 - B) r^-8, Eq. 2:
+// k q1 q2 / r^3); also returns 1/r, 1/r^2, 1/r^6 for the energies.  The Coulomb term
+// joins the LJ term in one fused multiply-add, so that no separate multiply feeds an
+// add (which a compiler could fuse in one kernel and not in another).
 __device__ __forceinline__ float pair_f(float r2, float A, float B, float kqq, float &ir,
                                         float &ir2, float &ir6)
 {
-    ir = rsqrt_nr(r2);
+    ir = rsqrt_hw(r2);
     ir2 = __fmul_rn(ir, ir);
     ir6 = __fmul_rn(__fmul_rn(ir2, ir2), ir2);
     const float ir8 = __fmul_rn(ir6, ir2);
-    const float lj = __fmaf_rn(A, __fmul_rn(ir8, ir6), -__fmul_rn(B, ir8));
+    const float lj = __fmul_rn(ir8, __fmaf_rn(A, ir6, -B));
     return __fmaf_rn(__fmul_rn(kqq, ir2), ir, lj);
 }
 
