@@ -255,13 +255,15 @@ int md_batch_step(int32_t nsys, const md_system_desc *systems, double *pos, doub
  *   2  half-shell kernel, 2 warps per block, 256 buffered pairs per warp
  *   3  half-shell kernel, 8 warps per block, 256 buffered pairs per warp
  *   4  half-shell kernel, 4 warps per block, 128 buffered pairs per warp
+ *   5  the cluster-pair kernel on a persistent grid: about one wave of blocks, each
+ *      taking cell pairs from a counter until none are left
  * The half-shell buffer holds the filter's survivors of one 32x32 block of candidate
  * pairs (the paper's queue between distance and force stages, Section IV); a block that
  * keeps more is processed in several passes.  More warps per block share the block's
  * staged cells among more candidate blocks; fewer give more blocks per SM for small
  * cells.
  */
-#define MD_BATCH_SHAPES 5
+#define MD_BATCH_SHAPES 6
 typedef struct md_batch_tuning {
     int32_t shape_regular; /* launch over the systems with >= 3 cells on every axis */
     int32_t shape_small;   /* launch over the systems with an axis of 2 cells */

@@ -32,7 +32,7 @@ FIXED_SCALE = 2.0**32
 EXPORTS = ("md_strerror", "md_abi_version", "md_cell_dims", "md_workspace_bytes", "md_build_cells",
            "md_build_cells_noalloc", "md_nonbonded_forces", "md_nonbonded_forces_algo", "md_step",
            "md_batch_workspace_bytes", "md_batch_prepare", "md_batch_step", "md_batch_step_tuned")
-BATCH_SHAPES = 5  # MD_BATCH_SHAPES: kernel shapes of the batched force launches
+BATCH_SHAPES = 6  # MD_BATCH_SHAPES: kernel shapes of the batched force launches
 
 _lib = None
 

@@ -122,6 +122,7 @@ WsLayout ws_layout(int n, int ncell)
     w.clu_pos_q = off;       off = align_up(off + sizeof(float4) * nn);
     w.clu_type = off;        off = align_up(off + sizeof(int32_t) * nn);
     w.clu_order = off;       off = align_up(off + sizeof(int32_t) * nn);
+    w.work = off;            off = align_up(off + 2 * sizeof(int32_t));
     w.total = off;
     return w;
 }

@@ -414,19 +414,19 @@ __device__ __forceinline__ void cluster_row(CluSmem<MODE> &sm, const float2 *s_a
     }
 }
 
+// One cell pair: cell cx of the launch (of gx) with stencil entry cy.
 template <int MODE, int STATS, bool BATCHED, bool MI>
-__global__ void __launch_bounds__(kCT, MODE == MD_ACCUM_FIXED64 ? 6 : 7)
-k_cluster(CluArgs a, BatchArgs bt, unsigned long long *sys_pair_count)
+__device__ __forceinline__ void cluster_item(CluSmem<MODE> &sm, float2 *s_ab, const CluArgs &a,
+                                             const BatchArgs &bt,
+                                             unsigned long long *sys_pair_count, int cx, int cy,
+                                             int gx)
 {
     using Acc = typename AccT<MODE>::T;
-    __shared__ __align__(16) CluSmem<MODE> sm;
-    extern __shared__ __align__(16) unsigned char s_dyn[];
-    float2 *s_ab = reinterpret_cast<float2 *>(s_dyn);  // LJ table [ntypes * ntypes]: (A, -B)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float e_lj = 0.f, e_c = 0.f, vir = 0.f;
     unsigned cnt = 0;
-    Partial *mine = a.partials + (size_t)blockIdx.y * gridDim.x;
+    Partial *mine = a.partials + (size_t)cy * gx;
 
     // the system this CTA works on: the only one, or the one its cell belongs to
     PairGeom g;
@@ -436,10 +436,10 @@ k_cluster(CluArgs a, BatchArgs bt, unsigned long long *sys_pair_count)
     int sid = 0;
     if (BATCHED) {
         // regular systems' cells first in cell_list, then those with a 2-cell axis
-        const int cell = bt.cell_list[(MI ? bt.ncell_reg : 0) + blockIdx.x];
+        const int cell = bt.cell_list[(MI ? bt.ncell_reg : 0) + cx];
         sid = bt.cell_sys[cell];
         const SysDesc &d = bt.sys[sid];
-        valid = cell_pair(d.box, cell - d.cell_offset, blockIdx.y, g);
+        valid = cell_pair(d.box, cell - d.cell_offset, cy, g);
         if (MI) {
 #pragma unroll
             for (int e = 0; e < 3; ++e) {
@@ -457,7 +457,7 @@ k_cluster(CluArgs a, BatchArgs bt, unsigned long long *sys_pair_count)
         k.rc2 = d.rc2;
         k.rc2m = d.rc2m;
     } else {
-        valid = cell_pair(a.box, blockIdx.x, blockIdx.y, g);
+        valid = cell_pair(a.box, cx, cy, g);
         if (MI) {
 #pragma unroll
             for (int e = 0; e < 3; ++e) {
@@ -474,13 +474,13 @@ k_cluster(CluArgs a, BatchArgs bt, unsigned long long *sys_pair_count)
         k.rc2m = a.rc2m;
     }
     if (!valid) {
-        if (STATS != kStatsNone) block_partial<kCT>(0.0, 0.0, 0.0, 0ull, mine);
+        if (STATS != kStatsNone) block_partial_to<kCT>(0.0, 0.0, 0.0, 0ull, mine + cx);
         return;
     }
     const int h_begin = a.cell_start[g.home], nh = a.cell_start[g.home + 1] - h_begin;
     const int n_begin = a.cell_start[g.nbr], nn = a.cell_start[g.nbr + 1] - n_begin;
     if (nh == 0 || nn == 0) {
-        if (STATS != kStatsNone) block_partial<kCT>(0.0, 0.0, 0.0, 0ull, mine);
+        if (STATS != kStatsNone) block_partial_to<kCT>(0.0, 0.0, 0.0, 0ull, mine + cx);
         return;
     }
     k.status = a.status;
@@ -600,9 +600,38 @@ k_cluster(CluArgs a, BatchArgs bt, unsigned long long *sys_pair_count)
         }
     }
     if (STATS != kStatsNone) {
-        block_partial<kCT>((double)e_lj, (double)e_c, (double)vir, (unsigned long long)cnt, mine);
-        if (BATCHED && sys_pair_count && threadIdx.x == 0 && mine[blockIdx.x].count)
-            atomicAdd(&sys_pair_count[sid], mine[blockIdx.x].count);
+        block_partial_to<kCT>((double)e_lj, (double)e_c, (double)vir, (unsigned long long)cnt, mine + cx);
+        if (BATCHED && sys_pair_count && threadIdx.x == 0 && mine[cx].count)
+            atomicAdd(&sys_pair_count[sid], mine[cx].count);
+    }
+}
+
+// One CTA per cell pair (grid cells x stencil entries), or PERSIST: a grid of about one
+// wave whose CTAs take cell pairs from a counter until none are left (`work`, zeroed
+// before the launch; items ordered stencil entry-major like the plain grid).
+template <int MODE, int STATS, bool BATCHED, bool MI, bool PERSIST>
+__global__ void __launch_bounds__(kCT, MODE == MD_ACCUM_FIXED64 ? 6 : 7)
+k_cluster(CluArgs a, BatchArgs bt, unsigned long long *sys_pair_count, int *work, int ncells,
+          int per_cell)
+{
+    __shared__ __align__(16) CluSmem<MODE> sm;
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    float2 *s_ab = reinterpret_cast<float2 *>(s_dyn);  // LJ table [ntypes * ntypes]: (A, -B)
+    if (!PERSIST) {
+        cluster_item<MODE, STATS, BATCHED, MI>(sm, s_ab, a, bt, sys_pair_count, blockIdx.x, blockIdx.y,
+                                               gridDim.x);
+        return;
+    }
+    __shared__ int s_item;
+    const int nitems = ncells * per_cell;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(work, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= nitems) break;
+        cluster_item<MODE, STATS, BATCHED, MI>(sm, s_ab, a, bt, sys_pair_count, item % ncells,
+                                               item / ncells, ncells);
     }
 }
 
@@ -648,16 +677,31 @@ k_finalize_clu(const void *__restrict__ accum, const int32_t *__restrict__ corde
     }
 }
 
-template <int MODE, int STATS, bool BATCHED = false, bool MI = false>
+// grid: cells x stencil entries.  PERSIST: the same items from about one wave of CTAs
+// (blocks per SM at this launch's shared memory x SMs), taking items from `work`.
+template <int MODE, int STATS, bool BATCHED = false, bool MI = false, bool PERSIST = false>
 void launch_cluster_t(const CluArgs &c, dim3 grid, cudaStream_t stream, const BatchArgs &b = BatchArgs{},
-                      unsigned long long *sys_pair_count = nullptr)
+                      unsigned long long *sys_pair_count = nullptr, int *work = nullptr)
 {
     const size_t dyn = sizeof(float2) * (size_t)c.ntypes * (size_t)c.ntypes;
     static const cudaError_t attr = cudaFuncSetAttribute(
-        k_cluster<MODE, STATS, BATCHED, MI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        k_cluster<MODE, STATS, BATCHED, MI, PERSIST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
         (int)(sizeof(float2) * kMaxTypes * kMaxTypes));
     (void)attr;
-    k_cluster<MODE, STATS, BATCHED, MI><<<grid, kCT, dyn, stream>>>(c, b, sys_pair_count);
+    dim3 g = grid;
+    if (PERSIST) {
+        // one wave at this launch's shared memory (host queries only; no stream work)
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cluster<MODE, STATS, BATCHED, MI, PERSIST>,
+                                                      kCT, dyn);
+        const long long wave = (long long)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+        const long long items = (long long)grid.x * grid.y;
+        g = dim3((unsigned)(items < wave ? items : wave), 1);
+    }
+    k_cluster<MODE, STATS, BATCHED, MI, PERSIST><<<g, kCT, dyn, stream>>>(c, b, sys_pair_count, work,
+                                                                        (int)grid.x, (int)grid.y);
 }
 
 template <int MODE, bool MI>
@@ -712,12 +756,22 @@ cudaError_t launch_cluster(const ForceArgs &a, const WsLayout &ws, char *wsp, Pa
     return launch_finalize_cluster(a, accum, ws, wsp, a.n, stream);
 }
 
+template <int MODE, bool MI, bool PERSIST>
+void launch_cluster_batched_t(const CluArgs &c, dim3 grid, cudaStream_t stream, const BatchArgs &b,
+                              unsigned long long *cnt, int *work)
+{
+    if (cnt) launch_cluster_t<MODE, kStatsCount, true, MI, PERSIST>(c, grid, stream, b, cnt, work);
+    else launch_cluster_t<MODE, kStatsNone, true, MI, PERSIST>(c, grid, stream, b, nullptr, work);
+}
+
 // Batched cluster kernel over the regular systems' cells (b.cell_list[0 .. ncell_reg),
 // 14 cell pairs each) or, mi, over those of the systems with a 2-cell axis (27 each).
+// persist_work: the persistent grid with this zeroed counter, else one CTA per pair.
 cudaError_t launch_cluster_batched(int mode, bool mi, const BatchArgs &b, const int32_t *cell_start,
                                    const float4 *pq, const int32_t *ty, void *accum,
                                    Partial *partials, uint32_t *status,
-                                   unsigned long long *sys_pair_count, cudaStream_t stream)
+                                   unsigned long long *sys_pair_count, int *persist_work,
+                                   cudaStream_t stream)
 {
     const int ncells = mi ? b.ncell_mi : b.ncell_reg;
     if (ncells <= 0) return cudaSuccess;
@@ -731,23 +785,18 @@ cudaError_t launch_cluster_batched(int mode, bool mi, const BatchArgs &b, const 
     c.partials = partials;
     c.status = status;
     dim3 grid(ncells, mi ? 27 : 14);
-    const bool cnt = sys_pair_count != nullptr;
-    if (mode == MD_ACCUM_FIXED64) {
-        if (mi) {
-            if (cnt) launch_cluster_t<MD_ACCUM_FIXED64, kStatsCount, true, true>(c, grid, stream, b, sys_pair_count);
-            else launch_cluster_t<MD_ACCUM_FIXED64, kStatsNone, true, true>(c, grid, stream, b, nullptr);
-        } else {
-            if (cnt) launch_cluster_t<MD_ACCUM_FIXED64, kStatsCount, true, false>(c, grid, stream, b, sys_pair_count);
-            else launch_cluster_t<MD_ACCUM_FIXED64, kStatsNone, true, false>(c, grid, stream, b, nullptr);
-        }
-    } else {
-        if (mi) {
-            if (cnt) launch_cluster_t<MD_ACCUM_F32, kStatsCount, true, true>(c, grid, stream, b, sys_pair_count);
-            else launch_cluster_t<MD_ACCUM_F32, kStatsNone, true, true>(c, grid, stream, b, nullptr);
-        } else {
-            if (cnt) launch_cluster_t<MD_ACCUM_F32, kStatsCount, true, false>(c, grid, stream, b, sys_pair_count);
-            else launch_cluster_t<MD_ACCUM_F32, kStatsNone, true, false>(c, grid, stream, b, nullptr);
-        }
+    unsigned long long *cnt = sys_pair_count;
+    int *w = persist_work;
+    const int sel = (mode == MD_ACCUM_FIXED64 ? 4 : 0) + (mi ? 2 : 0) + (w ? 1 : 0);
+    switch (sel) {
+    case 0: launch_cluster_batched_t<MD_ACCUM_F32, false, false>(c, grid, stream, b, cnt, w); break;
+    case 1: launch_cluster_batched_t<MD_ACCUM_F32, false, true>(c, grid, stream, b, cnt, w); break;
+    case 2: launch_cluster_batched_t<MD_ACCUM_F32, true, false>(c, grid, stream, b, cnt, w); break;
+    case 3: launch_cluster_batched_t<MD_ACCUM_F32, true, true>(c, grid, stream, b, cnt, w); break;
+    case 4: launch_cluster_batched_t<MD_ACCUM_FIXED64, false, false>(c, grid, stream, b, cnt, w); break;
+    case 5: launch_cluster_batched_t<MD_ACCUM_FIXED64, false, true>(c, grid, stream, b, cnt, w); break;
+    case 6: launch_cluster_batched_t<MD_ACCUM_FIXED64, true, false>(c, grid, stream, b, cnt, w); break;
+    default: launch_cluster_batched_t<MD_ACCUM_FIXED64, true, true>(c, grid, stream, b, cnt, w); break;
     }
     return cudaGetLastError();
 }

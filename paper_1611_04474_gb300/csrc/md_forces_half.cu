@@ -532,8 +532,8 @@ void launch_half_t(const HalfArgs &h, dim3 grid, cudaStream_t stream, const Batc
 
 // The half-shell shapes of the batched launches (md_batch_tuning): {warps per CTA,
 // survivors buffered per warp} = 1 {4, default}, 2 {2, 256}, 3 {8, 256}, 4 {4, 128}.
-// Shape 0 is the cluster kernel.
-static_assert(MD_BATCH_SHAPES == 5, "one case per shape");
+// Shape 0 is the cluster kernel and 5 the cluster kernel on a persistent grid.
+static_assert(MD_BATCH_SHAPES == 6, "one case per shape");
 
 template <int MODE, bool MI>
 void launch_batched_shape(int shape, const HalfArgs &h, dim3 grid, cudaStream_t stream,
@@ -575,6 +575,9 @@ cudaError_t launch_forces_batched(const ForceArgs &a, const BatchArgs &b,
     void *accum = wsp + ws.accum;
     cudaError_t e = cudaMemsetAsync(accum, 0, acc_bytes, stream);
     if (e != cudaSuccess) return e;
+    int *work = reinterpret_cast<int *>(wsp + ws.work);
+    if ((shape_reg == 5 || shape_mi == 5) && (e = cudaMemsetAsync(work, 0, 2 * sizeof(int), stream)) != cudaSuccess)
+        return e;
     // the batch's cells come from the fused MD-step build, already in cluster order;
     // both launches read them and accumulate in that order
     if (!a.presorted) return cudaErrorInvalidValue;
@@ -591,9 +594,9 @@ cudaError_t launch_forces_batched(const ForceArgs &a, const BatchArgs &b,
     if (b.ncell_reg > 0) {
         h.partials = partials;
         dim3 grid(b.ncell_reg, 14);
-        if (shape_reg == 0)
+        if (shape_reg == 0 || shape_reg == 5)
             e = launch_cluster_batched(a.mode, false, b, a.cell_start, h.pq, h.ty, accum, partials,
-                                       a.status, sys_pair_count, stream);
+                                       a.status, sys_pair_count, shape_reg == 5 ? work : nullptr, stream);
         else if (a.mode == MD_ACCUM_FIXED64) launch_batched_shape<MD_ACCUM_FIXED64, false>(shape_reg, h, grid, stream, b, sys_pair_count);
         else launch_batched_shape<MD_ACCUM_F32, false>(shape_reg, h, grid, stream, b, sys_pair_count);
         if (e != cudaSuccess) return e;
@@ -601,9 +604,9 @@ cudaError_t launch_forces_batched(const ForceArgs &a, const BatchArgs &b,
     if (b.ncell_mi > 0) {
         h.partials = partials + (size_t)14 * b.ncell_reg;
         dim3 grid(b.ncell_mi, 27);
-        if (shape_mi == 0)
+        if (shape_mi == 0 || shape_mi == 5)
             e = launch_cluster_batched(a.mode, true, b, a.cell_start, h.pq, h.ty, accum, h.partials,
-                                       a.status, sys_pair_count, stream);
+                                       a.status, sys_pair_count, shape_mi == 5 ? work + 1 : nullptr, stream);
         else if (a.mode == MD_ACCUM_FIXED64) launch_batched_shape<MD_ACCUM_FIXED64, true>(shape_mi, h, grid, stream, b, sys_pair_count);
         else launch_batched_shape<MD_ACCUM_F32, true>(shape_mi, h, grid, stream, b, sys_pair_count);
         if (e != cudaSuccess) return e;

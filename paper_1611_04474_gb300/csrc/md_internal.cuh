@@ -61,6 +61,7 @@ struct WsLayout {
     size_t ev;          // double[4]          energy/virial scratch of md_step
     size_t st_cell_start, st_perm, st_pos_q_sorted, st_type_sorted, st_pos_q;  // md_step only
     size_t clu_pos_q, clu_type, clu_order;  // cluster-pair kernel: per-cell reordered copies
+    size_t work;        // int[2] item counters of persistent force launches
     size_t total;
     int nslots;
 };
@@ -267,10 +268,10 @@ __device__ __forceinline__ T warp_sum(T v)
     return v;
 }
 
-// Sum (e_lj, e_c, w, count) over the block into partials[blockIdx.x] in a fixed order.
+// Sum (e_lj, e_c, w, count) over the block into *slot in a fixed order.
 template <int kThreads>
-__device__ __forceinline__ void block_partial(double e_lj, double e_c, double w,
-                                              unsigned long long cnt, Partial *partials)
+__device__ __forceinline__ void block_partial_to(double e_lj, double e_c, double w,
+                                                 unsigned long long cnt, Partial *slot)
 {
     __shared__ double s_e[3][kThreads / 32];
     __shared__ unsigned long long s_c[kThreads / 32];
@@ -294,8 +295,16 @@ __device__ __forceinline__ void block_partial(double e_lj, double e_c, double w,
             p.w += s_e[2][k];
             p.count += s_c[k];
         }
-        partials[blockIdx.x] = p;
+        *slot = p;
     }
+}
+
+// The same into partials[blockIdx.x].
+template <int kThreads>
+__device__ __forceinline__ void block_partial(double e_lj, double e_c, double w,
+                                              unsigned long long cnt, Partial *partials)
+{
+    block_partial_to<kThreads>(e_lj, e_c, w, cnt, partials + blockIdx.x);
 }
 
 }  // namespace mdnb
@@ -357,7 +366,8 @@ struct BatchArgs {
 cudaError_t launch_cluster_batched(int mode, bool mi, const BatchArgs &b, const int32_t *cell_start,
                                    const float4 *pq, const int32_t *ty, void *accum,
                                    Partial *partials, uint32_t *status,
-                                   unsigned long long *sys_pair_count, cudaStream_t stream);
+                                   unsigned long long *sys_pair_count, int *persist_work,
+                                   cudaStream_t stream);
 cudaError_t launch_kick_drift_build(double *pos, double *vel, const void *forces, int mode,
                                     const float *inv_mass, const float *q, const int32_t *type, int n,
                                     const BoxF &box_in, const BatchArgs *b, double dt, double half_dt,
