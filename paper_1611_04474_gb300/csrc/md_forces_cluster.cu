@@ -609,8 +609,18 @@ __device__ __forceinline__ void cluster_item(CluSmem<MODE> &sm, float2 *s_ab, co
 // One CTA per cell pair (grid cells x stencil entries), or PERSIST: a grid of about one
 // wave whose CTAs take cell pairs from a counter until none are left (`work`, zeroed
 // before the launch; items ordered stencil entry-major like the plain grid).
+// Register budget: 8 CTAs per SM (64 registers a thread), which the force, step and
+// pair-counting forms fit without spilling.  Summing energies carries more live values
+// (7 CTAs for FP32, 6 for FIXED64), and so does the persistent FIXED64 counting form (6).
+template <int MODE, int STATS, bool PERSIST>
+constexpr int clu_min_blocks()
+{
+    return STATS == kStatsEnergy ? (MODE == MD_ACCUM_FIXED64 ? 6 : 7)
+         : (MODE == MD_ACCUM_FIXED64 && STATS != kStatsNone && PERSIST) ? 6 : 8;
+}
+
 template <int MODE, int STATS, bool BATCHED, bool MI, bool PERSIST>
-__global__ void __launch_bounds__(kCT, MODE == MD_ACCUM_FIXED64 ? 6 : 7)
+__global__ void __launch_bounds__(kCT, (clu_min_blocks<MODE, STATS, PERSIST>()))
 k_cluster(CluArgs a, BatchArgs bt, unsigned long long *sys_pair_count, int *work, int ncells,
           int per_cell)
 {
