@@ -90,6 +90,9 @@ BoxF make_box(const double *L, const int32_t *dims)
         b.Llo[d] = (float)(L[d] - (double)b.Lhi[d]);
         b.invL[d] = (float)(1.0 / L[d]);
         b.inv_edge[d] = (double)dims[d] / L[d];
+        b.Lin[d] = (float)L[d];
+        if ((double)b.Lin[d] > L[d]) b.Lin[d] = nextafterf(b.Lin[d], 0.0f);
+        b.inv_edge_f[d] = (float)b.inv_edge[d];
         b.dims[d] = dims[d];
         prod *= dims[d];
     }
@@ -109,7 +112,7 @@ WsLayout ws_layout(int n, int ncell)
     w.nslots = slots;
     size_t off = 0;
     w.cell_id = off;         off = align_up(off + sizeof(int32_t) * nn);
-    w.cell_cnt = off;        off = align_up(off + sizeof(int32_t) * nc);
+    w.cell_cnt = off;        off = align_up(off + sizeof(int32_t) * (nc + 1));
     w.perm_tmp = off;        off = align_up(off + sizeof(int32_t) * nn);
     w.accum = off;           off = align_up(off + 32 * nn);
     w.partials = off;        off = align_up(off + sizeof(Partial) * (size_t)slots);
@@ -331,6 +334,7 @@ int md_step(double *pos, double *vel, void *forces, int32_t forces_valid, const 
     // the step's passes fused: [half kick +] drift + wrap + cell build in cluster order,
     // then the forces with the second half kick in their last pass
     a.presorted = 1;
+    a.accum_zeroed = mode != MD_ACCUM_F64;  // the build pass zeroes the accumulators
     a.kick_inv_mass = inv_mass;
     a.kick_half_dt = half_dt;
     auto build = [&](bool kick, double dt) -> cudaError_t {
@@ -486,6 +490,7 @@ int md_batch_step_tuned(int32_t nsys, const md_system_desc *systems, double *pos
     a.status = status;
     // the same fused passes as md_step, over the whole batch
     a.presorted = 1;
+    a.accum_zeroed = mode != MD_ACCUM_F64;  // the build pass zeroes the accumulators
     a.kick_inv_mass = inv_mass;
     a.kick_half_dt = half_dt;
     auto build = [&](bool kick, double dt) -> cudaError_t {

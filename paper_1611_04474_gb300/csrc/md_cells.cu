@@ -145,17 +145,58 @@ k_cell_sort(const int *__restrict__ cell_start, const int *__restrict__ perm_tmp
 
 // ---------------------------------------------------------------- fused MD-step passes
 
+// Exclusive scan of ncell <= kStepSmemCells counts by one block of kStepThreads: the
+// counts are staged in `s` (shared, ncell entries), cell_start[0..ncell] and the scatter
+// cursors (= cell_start[c], in place of the counts) are written.
+__device__ __forceinline__ void block_scan_cells(int *__restrict__ cnt_cursor, int ncell,
+                                                 int *__restrict__ cell_start, int *s)
+{
+    __shared__ int warp_sum[kStepThreads / 32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    for (int c = t; c < ncell; c += kStepThreads) s[c] = __ldcg(cnt_cursor + c);
+    __syncthreads();
+    const int per = (ncell + kStepThreads - 1) / kStepThreads;
+    const int lo = min(t * per, ncell), hi = min(lo + per, ncell);
+    int own = 0;
+    for (int c = lo; c < hi; ++c) own += s[c];
+    int incl = own;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += v;
+    }
+    if (lane == 31) warp_sum[warp] = incl;
+    __syncthreads();
+    int before = 0;
+#pragma unroll
+    for (int w = 0; w < kStepThreads / 32; ++w) before += w < warp ? warp_sum[w] : 0;
+    int run = before + incl - own;
+    for (int c = lo; c < hi; ++c) {
+        const int k = s[c];
+        cell_start[c] = run;
+        cnt_cursor[c] = run;
+        run += k;
+    }
+    if (t == kStepThreads - 1) cell_start[ncell] = before + incl;
+}
+
 // One velocity-Verlet half step per atom and its cell: v += dt/2 a (when kick), x <-
 // wrap(x + dt v), the float copy (x, y, z, q), the cell index and the histogram; the
 // work of k_kick, k_drift_wrap and k_cell_index in one pass.  BATCHED: each atom's box
-// from its system, cells numbered over the batch.
+// from its system, cells numbered over the batch.  It also zeroes the force kernels'
+// cluster-order accumulators (`accum`, MD_ACCUM_F32 float4[n] or MD_ACCUM_FIXED64
+// u64[3][n]; null for none) and the persistent launches' item counters (`work`, may be
+// null).  SMEM (ncell <= kStepSmemCells): the last block to finish also scans the
+// histogram into cell_start and the scatter cursors; cell_cnt[ncell] counts finished
+// blocks and must be zero at launch.
 template <bool SMEM, bool BATCHED>
 __global__ void __launch_bounds__(kStepThreads)
 k_kick_drift_index(double *__restrict__ pos, double *__restrict__ vel, const void *__restrict__ forces,
                    int mode, const float *__restrict__ inv_mass, const float *__restrict__ q, int n,
                    BoxF box_in, BatchArgs b, double dt, double half_dt, int kick,
                    float4 *__restrict__ pos_q_out, int *__restrict__ cell_id,
-                   int *__restrict__ cell_cnt, uint32_t *status)
+                   int *__restrict__ cell_cnt, int *__restrict__ cell_start, void *__restrict__ accum,
+                   int *__restrict__ work, uint32_t *status)
 {
     extern __shared__ int s_hist[];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -164,8 +205,19 @@ k_kick_drift_index(double *__restrict__ pos, double *__restrict__ vel, const voi
         for (int t = threadIdx.x; t < ncell; t += blockDim.x) s_hist[t] = 0;
         __syncthreads();
     }
+    if (work && i < 2) work[i] = 0;
     int c = -1;
     if (i < n) {
+        if (accum) {
+            if (mode == MD_ACCUM_F32) {
+                reinterpret_cast<float4 *>(accum)[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            } else {
+                unsigned long long *A = reinterpret_cast<unsigned long long *>(accum);
+                A[i] = 0ull;
+                A[(size_t)n + i] = 0ull;
+                A[2 * (size_t)n + i] = 0ull;
+            }
+        }
         const SysDesc *d = BATCHED ? &b.sys[b.atom_sys[i]] : nullptr;
         const BoxF &box = BATCHED ? d->box : box_in;
         double v[3] = {vel[3 * i], vel[3 * i + 1], vel[3 * i + 2]};
@@ -184,10 +236,11 @@ k_kick_drift_index(double *__restrict__ pos, double *__restrict__ vel, const voi
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             double w = drift_coord(pos[3 * i + k], v[k], dt);
-            if (isfinite(w)) {
-                w = wrap_coord(w, box.L[k]);
-            } else {
-                ok = false;
+            if (!in_box_f64(w, box.L[k])) {
+                if (isfinite(w))
+                    w = wrap_coord(w, box.L[k]);
+                else
+                    ok = false;
             }
             x[k] = w;
             pos[3 * i + k] = w;
@@ -207,6 +260,17 @@ k_kick_drift_index(double *__restrict__ pos, double *__restrict__ vel, const voi
         __syncthreads();
         for (int t = threadIdx.x; t < ncell; t += blockDim.x)
             if (s_hist[t]) atomicAdd(&cell_cnt[t], s_hist[t]);
+        // the last block to finish scans the counts (each block's adds are made visible
+        // before it is counted)
+        __shared__ int s_last;
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) s_last = atomicAdd(&cell_cnt[ncell], 1) == (int)gridDim.x - 1;
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            block_scan_cells(cell_cnt, ncell, cell_start, s_hist);
+        }
     } else {
         const unsigned act = __ballot_sync(0xffffffffu, c >= 0);
         const unsigned grp = __match_any_sync(0xffffffffu, c) & act;
@@ -215,12 +279,16 @@ k_kick_drift_index(double *__restrict__ pos, double *__restrict__ vel, const voi
 }
 
 constexpr int kClusterSortMax = 1024;  // cells with more members keep ascending input order
+constexpr int kClusterCols = 64;       // at most 8 x 8 columns per cell
 
 // One block per cell: the members straight into the force kernel's cluster order --
 // columns of an S x S grid over the cell's x-y face, z along each column (alternating),
 // ties by input index -- with the outputs of the cell build in that order (perm maps a
 // slot to its input index).  This is a valid cell list (each cell contiguous); only the
-// order within a cell differs from k_cell_sort's ascending input order.
+// order within a cell differs from k_cell_sort's ascending input order.  The members
+// are counted per column and each is ranked only against its own column's keys.  The
+// order needs no particular rounding, only the same one every run, so the keys are
+// formed in FP32.
 template <bool BATCHED>
 __global__ void __launch_bounds__(kSortThreads)
 k_sort_cluster(const int *__restrict__ cell_start, const int *__restrict__ perm_tmp,
@@ -228,7 +296,10 @@ k_sort_cluster(const int *__restrict__ cell_start, const int *__restrict__ perm_
                BatchArgs b, int32_t *__restrict__ perm, float4 *__restrict__ pos_q_sorted,
                int32_t *__restrict__ type_sorted)
 {
-    __shared__ unsigned long long s_key[kClusterSortMax];
+    __shared__ unsigned long long s_key[kClusterSortMax];  // by arrival
+    __shared__ unsigned long long s_bkt[kClusterSortMax];  // grouped by column
+    __shared__ int s_col[kClusterCols + 1];                // counts, then column starts
+    __shared__ int s_fill[kClusterCols];
     const int cg = blockIdx.x;
     const BoxF &box = BATCHED ? b.sys[b.cell_sys[cg]].box : box_in;
     const int c = BATCHED ? cg - b.sys[b.cell_sys[cg]].cell_offset : cg;
@@ -257,26 +328,55 @@ k_sort_cluster(const int *__restrict__ cell_start, const int *__restrict__ perm_
     const int nx = box.dims[0], ny = box.dims[1];
     const int cx = c % nx, cy = (c / nx) % ny, cz = c / (nx * ny);
     const int S = max(1, min(8, (int)(sqrtf((float)m * (1.0f / 20.0f)) + 0.5f)));
+    const int ncol = S * S;
+    for (int t = threadIdx.x; t < ncol; t += kSortThreads) {
+        s_col[t] = 0;
+        s_fill[t] = 0;
+    }
+    __syncthreads();
+    const float fS = (float)S;
     for (int t = threadIdx.x; t < m; t += kSortThreads) {
         const int e = perm_tmp[s0 + t];
-        const float4 p = pos_q[e];
-        const double ux = wrap_coord((double)p.x, box.L[0]) * box.inv_edge[0] - cx;
-        const double uy = wrap_coord((double)p.y, box.L[1]) * box.inv_edge[1] - cy;
-        double uz = wrap_coord((double)p.z, box.L[2]) * box.inv_edge[2] - cz;
-        const int kx = min(S - 1, max(0, (int)(ux * S))), ky = min(S - 1, max(0, (int)(uy * S)));
+        const float4 p = wrap_pos_f(pos_q[e], box);
+        // position in cell units, clamped onto the cell's faces
+        const float ux = __fsub_rn(__fmul_rn(p.x, box.inv_edge_f[0]), (float)cx);
+        const float uy = __fsub_rn(__fmul_rn(p.y, box.inv_edge_f[1]), (float)cy);
+        float uz = __fsub_rn(__fmul_rn(p.z, box.inv_edge_f[2]), (float)cz);
+        const int kx = min(S - 1, max(0, (int)__fmul_rn(ux, fS)));
+        const int ky = min(S - 1, max(0, (int)__fmul_rn(uy, fS)));
         const int col = ky * S + ((ky & 1) ? S - 1 - kx : kx);  // boustrophedon
-        uz = fmin(fmax(uz, 0.0), 1.0);
-        if (col & 1) uz = 1.0 - uz;
-        const unsigned long long zq = (unsigned long long)(uz * 16777215.0);  // 24 bits
+        uz = fminf(fmaxf(uz, 0.0f), 1.0f);
+        if (col & 1) uz = __fsub_rn(1.0f, uz);
+        const unsigned long long zq = (unsigned long long)(unsigned)__fmul_rn(uz, 16777215.0f);  // 24 bits
         // finite coordinates only matter for the order; e keeps the keys distinct
         s_key[t] = ((unsigned long long)col << 54) | (zq << 30) | (unsigned long long)e;
+        atomicAdd(&s_col[col], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int k = 0; k < ncol; ++k) {
+            const int v = s_col[k];
+            s_col[k] = run;
+            run += v;
+        }
+        s_col[ncol] = run;
     }
     __syncthreads();
     for (int t = threadIdx.x; t < m; t += kSortThreads) {
         const unsigned long long key = s_key[t];
+        const int col = (int)(key >> 54);
+        s_bkt[s_col[col] + atomicAdd(&s_fill[col], 1)] = key;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < m; t += kSortThreads) {
+        const unsigned long long key = s_key[t];
+        const int col = (int)(key >> 54);
+        const int b0 = s_col[col], b1 = s_col[col + 1];
         int rank = 0;
-        for (int u = 0; u < m; ++u) rank += s_key[u] < key;
-        place((int)(key & ((1ull << 30) - 1)), s0 + rank, pos_q, type, box, perm, pos_q_sorted, type_sorted);
+        for (int u = b0; u < b1; ++u) rank += s_bkt[u] < key;
+        place((int)(key & ((1ull << 30) - 1)), s0 + b0 + rank, pos_q, type, box, perm, pos_q_sorted,
+              type_sorted);
     }
 }
 
@@ -324,24 +424,28 @@ cudaError_t launch_kick_drift_build(double *pos, double *vel, const void *forces
     int *cell_id = reinterpret_cast<int *>(wsp + ws.cell_id);
     int *cnt = reinterpret_cast<int *>(wsp + ws.cell_cnt);
     int *perm_tmp = reinterpret_cast<int *>(wsp + ws.perm_tmp);
+    void *accum = mode == MD_ACCUM_F64 ? nullptr : static_cast<void *>(wsp + ws.accum);
+    int *work = reinterpret_cast<int *>(wsp + ws.work);
     const int ncell = b ? b->ncell : box_in.ncell;
     const BatchArgs nob = {};
     const BatchArgs &bb = b ? *b : nob;
-    cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)ncell, stream);
+    // the counts and the finished-block counter
+    cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int) * ((size_t)ncell + 1), stream);
     if (e != cudaSuccess) return e;
+    const size_t sm = ncell <= kStepSmemCells ? sizeof(int) * (size_t)ncell : 0;
     if (n > 0) {
         const int g = (n + kStepThreads - 1) / kStepThreads;
-        const size_t sm = ncell <= kStepSmemCells ? sizeof(int) * (size_t)ncell : 0;
         const int k = kick ? 1 : 0;
         if (b) {
-            if (sm) k_kick_drift_index<true, true><<<g, kStepThreads, sm, stream>>>(pos, vel, forces, mode, inv_mass, q, n, box_in, bb, dt, half_dt, k, pos_q, cell_id, cnt, status);
-            else k_kick_drift_index<false, true><<<g, kStepThreads, 0, stream>>>(pos, vel, forces, mode, inv_mass, q, n, box_in, bb, dt, half_dt, k, pos_q, cell_id, cnt, status);
+            if (sm) k_kick_drift_index<true, true><<<g, kStepThreads, sm, stream>>>(pos, vel, forces, mode, inv_mass, q, n, box_in, bb, dt, half_dt, k, pos_q, cell_id, cnt, cell_start, accum, work, status);
+            else k_kick_drift_index<false, true><<<g, kStepThreads, 0, stream>>>(pos, vel, forces, mode, inv_mass, q, n, box_in, bb, dt, half_dt, k, pos_q, cell_id, cnt, cell_start, accum, work, status);
         } else {
-            if (sm) k_kick_drift_index<true, false><<<g, kStepThreads, sm, stream>>>(pos, vel, forces, mode, inv_mass, q, n, box_in, bb, dt, half_dt, k, pos_q, cell_id, cnt, status);
-            else k_kick_drift_index<false, false><<<g, kStepThreads, 0, stream>>>(pos, vel, forces, mode, inv_mass, q, n, box_in, bb, dt, half_dt, k, pos_q, cell_id, cnt, status);
+            if (sm) k_kick_drift_index<true, false><<<g, kStepThreads, sm, stream>>>(pos, vel, forces, mode, inv_mass, q, n, box_in, bb, dt, half_dt, k, pos_q, cell_id, cnt, cell_start, accum, work, status);
+            else k_kick_drift_index<false, false><<<g, kStepThreads, 0, stream>>>(pos, vel, forces, mode, inv_mass, q, n, box_in, bb, dt, half_dt, k, pos_q, cell_id, cnt, cell_start, accum, work, status);
         }
     }
-    k_scan_cells<<<1, kScanThreads, 0, stream>>>(cnt, ncell, cell_start);
+    // the shared-histogram form scans in its last block
+    if (n == 0 || !sm) k_scan_cells<<<1, kScanThreads, 0, stream>>>(cnt, ncell, cell_start);
     if (n > 0) {
         const int g = (n + kIndexThreads - 1) / kIndexThreads;
         k_scatter<<<g, kIndexThreads, 0, stream>>>(cell_id, n, cnt, perm_tmp);

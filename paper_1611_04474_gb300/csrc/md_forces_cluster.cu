@@ -732,7 +732,7 @@ cudaError_t launch_cluster(const ForceArgs &a, const WsLayout &ws, char *wsp, Pa
     float4 *cpq = reinterpret_cast<float4 *>(wsp + ws.clu_pos_q);
     int32_t *cty = reinterpret_cast<int32_t *>(wsp + ws.clu_type);
     int32_t *corder = reinterpret_cast<int32_t *>(wsp + ws.clu_order);
-    cudaError_t e = cudaMemsetAsync(accum, 0, acc_bytes, stream);
+    cudaError_t e = a.accum_zeroed ? cudaSuccess : cudaMemsetAsync(accum, 0, acc_bytes, stream);
     if (e != cudaSuccess) return e;
     if (!a.presorted)
         k_cluster_order<<<a.box.ncell, kOrderThreads, 0, stream>>>(a.cell_start, a.pos_q_sorted,

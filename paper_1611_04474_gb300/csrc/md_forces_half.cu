@@ -573,10 +573,11 @@ cudaError_t launch_forces_batched(const ForceArgs &a, const BatchArgs &b,
     Partial *partials = reinterpret_cast<Partial *>(wsp + ws.partials);
     const size_t acc_bytes = (size_t)b.n * (a.mode == MD_ACCUM_FIXED64 ? 24 : 16);
     void *accum = wsp + ws.accum;
-    cudaError_t e = cudaMemsetAsync(accum, 0, acc_bytes, stream);
+    cudaError_t e = a.accum_zeroed ? cudaSuccess : cudaMemsetAsync(accum, 0, acc_bytes, stream);
     if (e != cudaSuccess) return e;
     int *work = reinterpret_cast<int *>(wsp + ws.work);
-    if ((shape_reg == 5 || shape_mi == 5) && (e = cudaMemsetAsync(work, 0, 2 * sizeof(int), stream)) != cudaSuccess)
+    if (!a.accum_zeroed && (shape_reg == 5 || shape_mi == 5) &&
+        (e = cudaMemsetAsync(work, 0, 2 * sizeof(int), stream)) != cudaSuccess)
         return e;
     // the batch's cells come from the fused MD-step build, already in cluster order;
     // both launches read them and accumulate in that order

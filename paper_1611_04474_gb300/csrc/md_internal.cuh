@@ -31,6 +31,8 @@ struct BoxF {
     float Llo[3];   // float(L - Lhi): the remainder, so Lhi + Llo == L to ~2^-48 L
     float invL[3];  // 1/L rounded to float
     double inv_edge[3];  // dims / L (one IEEE division, the same bits on host and device)
+    float Lin[3];        // the largest float <= L: x in [0, Lin) means (double)x in [0, L)
+    float inv_edge_f[3]; // inv_edge rounded to float
     int dims[3];
     int ncell;
 };
@@ -54,7 +56,8 @@ struct SysDesc {
 
 struct WsLayout {
     size_t cell_id;     // int32 [n]          cell of each input atom
-    size_t cell_cnt;    // int32 [ncell]      per-cell counts, then scatter cursors
+    size_t cell_cnt;    // int32 [ncell + 1]  per-cell counts, then scatter cursors; the last
+                        //                    counts the finished blocks of the step's build pass
     size_t perm_tmp;    // int32 [n]          unsorted slot -> input index
     size_t accum;       // 32 B x n           sorted-order force accumulators
     size_t partials;    // Partial [nslots]
@@ -87,12 +90,22 @@ __device__ __forceinline__ void set_status(uint32_t *status, uint32_t bits)
     if (status) atomicOr(status, bits);
 }
 
+// 0 <= x < L for a finite L > 0, decided on the bit patterns (non-negative doubles
+// order like their bits), which keeps the test off the FP64 pipe.  -0.0 is inside, as
+// for the floating-point comparison; NaN and infinities are not.
+__device__ __forceinline__ bool in_box_f64(double x, double L)
+{
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long a = u & 0x7fffffffffffffffull;
+    return (u == a || a == 0ull) && a < (unsigned long long)__double_as_longlong(L);
+}
+
 // Wrap a coordinate into [0, L) in FP64 (the documented rule).  A coordinate already
 // in [0, L) is returned as it is, which is what the rule gives for it (even when x/L
 // rounds up to 1, the fold-back restores x exactly), without the FP64 division.
 __device__ __forceinline__ double wrap_coord(double x, double L)
 {
-    if (x >= 0.0 && x < L) return x;
+    if (in_box_f64(x, L)) return x;
     double w = x - L * floor(x / L);
     if (w < 0.0) w += L;
     if (w >= L) w -= L;
@@ -112,18 +125,38 @@ __device__ __forceinline__ bool finite3(double x, double y, double z)
     return isfinite(x) && isfinite(y) && isfinite(z);
 }
 
+// Cell index along axis k of a float coordinate, equal to
+// cell_coord(wrap_coord((double)x, L), ...) for every x.  For x in [0, Lin) the FP32
+// product t = x * (n/L) decides unless it lies within 2.5e-7 t of an integer: the FP32
+// and FP64 products differ by less than 1.2e-7 t (two float roundings, of n/L and of
+// the product), so outside that band both have the same floor.  Inside it, and for x
+// outside [0, Lin), the FP64 rule runs.
+__device__ __forceinline__ int cell_coord_fast(float x, const BoxF &box, int k)
+{
+    if (x >= 0.0f && x < box.Lin[k]) {
+        const float t = __fmul_rn(x, box.inv_edge_f[k]);
+        const float fl = floorf(t);
+        const float fr = __fsub_rn(t, fl);  // exact (Sterbenz for t >= 1; fl = 0 below)
+        const float tol = __fmul_rn(t, 2.5e-7f);
+        if (fr > tol && fr < __fsub_rn(1.0f, tol)) {
+            const int c = (int)fl;
+            return c < box.dims[k] ? c : box.dims[k] - 1;
+        }
+    }
+    return cell_coord(wrap_coord((double)x, box.L[k]), box.dims[k], box.inv_edge[k]);
+}
+
 // Cell of a float position under the documented rule (FP64 wrap of the float value,
 // floor(w * n/L) clamped); a non-finite coordinate sets the status and gives cell 0.
 __device__ __forceinline__ int cell_of(const float4 &p, const BoxF &box, uint32_t *status)
 {
-    double x = p.x, y = p.y, z = p.z;
-    if (!finite3(x, y, z)) {
+    if (!(isfinite(p.x) && isfinite(p.y) && isfinite(p.z))) {
         set_status(status, MD_STATUS_NONFINITE);
         return 0;
     }
-    int cx = cell_coord(wrap_coord(x, box.L[0]), box.dims[0], box.inv_edge[0]);
-    int cy = cell_coord(wrap_coord(y, box.L[1]), box.dims[1], box.inv_edge[1]);
-    int cz = cell_coord(wrap_coord(z, box.L[2]), box.dims[2], box.inv_edge[2]);
+    const int cx = cell_coord_fast(p.x, box, 0);
+    const int cy = cell_coord_fast(p.y, box, 1);
+    const int cz = cell_coord_fast(p.z, box, 2);
     return cx + box.dims[0] * (cy + box.dims[1] * cz);
 }
 
@@ -139,6 +172,26 @@ __device__ __forceinline__ double drift_coord(double x, double v, double dt)
     return __dadd_rn(x, __dmul_rn(dt, v));
 }
 
+// A float position wrapped into the box by the FP64 rule and rounded back to float
+// (non-finite coordinates give the origin); the charge is kept.  A coordinate in
+// [0, Lin) wraps to itself, so the FP64 work runs only for the rare others.
+__device__ __forceinline__ float4 wrap_pos_f(const float4 &p, const BoxF &box)
+{
+    float4 o = p;
+    if (!(p.x >= 0.0f && p.x < box.Lin[0] && p.y >= 0.0f && p.y < box.Lin[1] && p.z >= 0.0f &&
+          p.z < box.Lin[2])) {
+        const double x = p.x, y = p.y, z = p.z;
+        if (isfinite(x) && isfinite(y) && isfinite(z)) {
+            o.x = (float)wrap_coord(x, box.L[0]);
+            o.y = (float)wrap_coord(y, box.L[1]);
+            o.z = (float)wrap_coord(z, box.L[2]);
+        } else {
+            o.x = o.y = o.z = 0.0f;
+        }
+    }
+    return o;
+}
+
 // Sorted-order slot of one atom: its input index, its wrapped float position and
 // charge, its type (the outputs of the cell build).
 __device__ __forceinline__ void place(int e, int slot, const float4 *__restrict__ pos_q,
@@ -147,18 +200,7 @@ __device__ __forceinline__ void place(int e, int slot, const float4 *__restrict_
                                       int32_t *__restrict__ type_sorted)
 {
     perm[slot] = e;
-    const float4 p = pos_q[e];
-    const double x = p.x, y = p.y, z = p.z;
-    float4 o;
-    if (isfinite(x) && isfinite(y) && isfinite(z)) {
-        o.x = (float)wrap_coord(x, box.L[0]);
-        o.y = (float)wrap_coord(y, box.L[1]);
-        o.z = (float)wrap_coord(z, box.L[2]);
-    } else {
-        o.x = o.y = o.z = 0.0f;
-    }
-    o.w = p.w;
-    pos_q_sorted[slot] = o;
+    pos_q_sorted[slot] = wrap_pos_f(pos_q[e], box);
     type_sorted[slot] = type[e];
 }
 
@@ -338,6 +380,9 @@ struct ForceArgs {
     // within-cell order already the cluster kernel's (from the fused MD-step build):
     // no ordering pass, perm maps each slot to its input index
     int presorted = 0;
+    // the build pass of the MD step already zeroed the cluster-order accumulators (and
+    // the persistent launches' item counters)
+    int accum_zeroed = 0;
     // optional half kick v += dt/2 a(F) applied as the forces are written (MD step)
     double *kick_vel = nullptr;
     const float *kick_inv_mass = nullptr;

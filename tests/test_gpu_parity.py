@@ -74,6 +74,56 @@ def test_cells_identical_to_oracle(cuda_lib, name):
     assert int(eng.status.item()) == 0
 
 
+def _face_coords(L, n, rng, count):
+    """float32 coordinates on and next to the cell faces k L / n (k = 0..n), plus -0.0,
+    float(L) and coordinates outside [0, L) that the build must wrap."""
+    vals = []
+    for k in range(n + 1):
+        f = np.float32(k * L / n)
+        up = np.nextafter(f, np.float32(np.inf))
+        vals += [f, up, np.nextafter(up, np.float32(np.inf)), np.nextafter(f, np.float32(-np.inf))]
+    vals += [np.float32(-0.0), np.float32(L), np.float32(-1e-7), np.float32(L + 1e-3),
+             np.float32(-L + 0.5), np.float32(2.5 * L)]
+    vals = np.array(vals, np.float32)
+    return vals[rng.integers(0, len(vals), count)]
+
+
+def _wrap_f32(x, L):
+    """The documented wrap of float coordinates in FP64, rounded back to float."""
+    x = x.astype(np.float64)
+    w = np.where((x >= 0.0) & (x < L), x, x - L * np.floor(x / L))
+    w = np.where(w < 0.0, w + L, w)
+    w = np.where(w >= L, w - L, w)
+    return w.astype(np.float32)
+
+
+@pytest.mark.parametrize("box,rc", [((36.0, 37.3, 48.0001), 12.0), ((24.0, 25.2, 26.4), 4.0),
+                                    ((10.1, 7.0, 13.37), 3.4)])
+def test_cells_on_cell_faces(cuda_lib, box, rc):
+    """Coordinates on, one and two float steps beside every cell face, and outside the
+    box: the cell of each atom is decided exactly as the oracle's FP64 rule decides it."""
+    api = cuda_lib
+    s = W.small_random(900, box, rc=rc, seed=11)
+    rng = np.random.default_rng(12)
+    dims = oracle.cell_dims(np.array(box), rc)
+    pos = s.pos.copy()
+    for k in range(3):
+        sel = rng.random(len(pos)) < 0.8
+        pos[sel, k] = _face_coords(box[k], dims[k], rng, int(sel.sum()))
+    s.pos = pos
+    eng = api.Engine(s)
+    eng.build_cells()
+    torch.cuda.synchronize()
+    dims_o, cell_of, cell_start, order = oracle.build_cells(pos.astype(np.float64), s.box, s.rc)
+    assert list(dims_o) == eng.dims
+    np.testing.assert_array_equal(eng.cells.cell_start.cpu().numpy(), cell_start)
+    np.testing.assert_array_equal(eng.cells.perm.cpu().numpy(), order)
+    pqs = eng.cells.pos_q_sorted.cpu().numpy()
+    for k in range(3):
+        np.testing.assert_array_equal(pqs[:, k], _wrap_f32(pos[order, k], box[k]))
+    assert int(eng.status.item()) == 0
+
+
 @pytest.mark.parametrize("name", list(SYSTEMS))
 @pytest.mark.parametrize("mode", [0, 1, 2])
 def test_forces_match_oracle(cuda_lib, name, mode):
