@@ -443,10 +443,10 @@ def run_ours(args):
     sm_clock_ghz = 2.07
     peak_tflops = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_clock_ghz / 1e3
     achieved = flops / (t_force / 1e3) / 1e12
-    # per MD step: kick + drift + wrap + cell index (+ scan of the cell counts in its last
-    # block), scatter, cell sort into cluster order, force kernel, finalize + kick
+    # per MD step: kick + drift + wrap + cell index and bin (+ scan of the cell counts in
+    # its last block), cell sort into cluster order, force kernel, finalize + kick
     # (md_step always runs the default kernel); the counts are zeroed by a memset
-    per_step_launches = 5
+    per_step_launches = 4
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step / args.steps, "higher_is_better": True,

@@ -100,7 +100,14 @@ BoxF make_box(const double *L, const int32_t *dims)
     return b;
 }
 
-WsLayout ws_layout(int n, int ncell)
+int bin_capacity(int n, int ncell)
+{
+    const long long mean = ((long long)n + ncell - 1) / (ncell > 0 ? ncell : 1);
+    const long long cap = (2 * mean + 64 + 31) / 32 * 32;
+    return (int)(cap < (1LL << 30) ? cap : (1LL << 30));
+}
+
+WsLayout ws_layout(int n, int ncell, bool bins)
 {
     WsLayout w;
     size_t nn = (size_t)(n > 0 ? n : 1);
@@ -126,6 +133,8 @@ WsLayout ws_layout(int n, int ncell)
     w.clu_type = off;        off = align_up(off + sizeof(int32_t) * nn);
     w.clu_order = off;       off = align_up(off + sizeof(int32_t) * nn);
     w.work = off;            off = align_up(off + 2 * sizeof(int32_t));
+    w.bin_cap = bins && n > 0 ? bin_capacity(n, (int)nc) : 0;
+    w.bins = off;            off = align_up(off + sizeof(int32_t) * nc * (size_t)w.bin_cap);
     w.total = off;
     return w;
 }
@@ -160,7 +169,7 @@ static int batch_layout(int32_t nsys, const md_system_desc *systems, BatchLayout
     bl->cell_sys = off;  off = align_up(off + sizeof(int) * (size_t)ncell);
     bl->cell_list = off; off = align_up(off + sizeof(int) * (size_t)ncell);
     bl->atom_sys = off;  off = align_up(off + sizeof(int) * (size_t)(n > 0 ? n : 1));
-    bl->run = ws_layout((int)n, (int)ncell);
+    bl->run = ws_layout((int)n, (int)ncell, false);
     bl->run_base = off;
     bl->total = off + bl->run.total;
     return MD_OK;

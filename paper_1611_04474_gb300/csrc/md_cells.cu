@@ -188,7 +188,9 @@ __device__ __forceinline__ void block_scan_cells(int *__restrict__ cnt_cursor, i
 // u64[3][n]; null for none) and the persistent launches' item counters (`work`, may be
 // null).  SMEM (ncell <= kStepSmemCells): the last block to finish also scans the
 // histogram into cell_start and the scatter cursors; cell_cnt[ncell] counts finished
-// blocks and must be zero at launch.
+// blocks and must be zero at launch.  bin_cap > 0: each atom also takes a slot of its
+// cell's bin (bins[c][0..bin_cap), by arrival; the count atomics hand out the slots),
+// which replaces the scatter pass; members past bin_cap are not binned.
 template <bool SMEM, bool BATCHED>
 __global__ void __launch_bounds__(kStepThreads)
 k_kick_drift_index(double *__restrict__ pos, double *__restrict__ vel, const void *__restrict__ forces,
@@ -196,7 +198,7 @@ k_kick_drift_index(double *__restrict__ pos, double *__restrict__ vel, const voi
                    BoxF box_in, BatchArgs b, double dt, double half_dt, int kick,
                    float4 *__restrict__ pos_q_out, int *__restrict__ cell_id,
                    int *__restrict__ cell_cnt, int *__restrict__ cell_start, void *__restrict__ accum,
-                   int *__restrict__ work, uint32_t *status)
+                   int *__restrict__ work, int *__restrict__ bins, int bin_cap, uint32_t *status)
 {
     extern __shared__ int s_hist[];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -251,15 +253,32 @@ k_kick_drift_index(double *__restrict__ pos, double *__restrict__ vel, const voi
         c = (BATCHED ? d->cell_offset : 0) + cell_of(p, box, status);
         cell_id[i] = c;
     }
+    const int lane = threadIdx.x & 31;
+    const unsigned act = __ballot_sync(0xffffffffu, c >= 0);
+    const unsigned grp = __match_any_sync(0xffffffffu, c) & act;
+    const int leader = __ffs(grp) - 1;
+    const int below = __popc(grp & ((1u << lane) - 1u));  // members of the group before this lane
     if (SMEM) {
         // one shared atomic per distinct cell of the warp (consecutive atoms often share
-        // a cell)
-        const unsigned act = __ballot_sync(0xffffffffu, c >= 0);
-        const unsigned grp = __match_any_sync(0xffffffffu, c) & act;
-        if (c >= 0 && (threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&s_hist[c], __popc(grp));
+        // a cell), then one global atomic per cell of the block
+        int wb = 0;
+        if (c >= 0 && lane == leader) wb = atomicAdd(&s_hist[c], __popc(grp));
+        wb = __shfl_sync(0xffffffffu, wb, leader < 0 ? 0 : leader);
         __syncthreads();
-        for (int t = threadIdx.x; t < ncell; t += blockDim.x)
-            if (s_hist[t]) atomicAdd(&cell_cnt[t], s_hist[t]);
+        for (int t = threadIdx.x; t < ncell; t += blockDim.x) {
+            const int v = s_hist[t];
+            if (v) {
+                const int base = atomicAdd(&cell_cnt[t], v);
+                if (bin_cap) s_hist[t] = base;  // the block's first slot in cell t
+            }
+        }
+        if (bin_cap) {
+            __syncthreads();
+            if (c >= 0) {
+                const int off = s_hist[c] + wb + below;
+                if (off < bin_cap) bins[(size_t)c * bin_cap + off] = i;
+            }
+        }
         // the last block to finish scans the counts (each block's adds are made visible
         // before it is counted)
         __shared__ int s_last;
@@ -272,9 +291,13 @@ k_kick_drift_index(double *__restrict__ pos, double *__restrict__ vel, const voi
             block_scan_cells(cell_cnt, ncell, cell_start, s_hist);
         }
     } else {
-        const unsigned act = __ballot_sync(0xffffffffu, c >= 0);
-        const unsigned grp = __match_any_sync(0xffffffffu, c) & act;
-        if (c >= 0 && (threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&cell_cnt[c], __popc(grp));
+        int base = 0;
+        if (c >= 0 && lane == leader) base = atomicAdd(&cell_cnt[c], __popc(grp));
+        base = __shfl_sync(0xffffffffu, base, leader < 0 ? 0 : leader);
+        if (bin_cap && c >= 0) {
+            const int off = base + below;
+            if (off < bin_cap) bins[(size_t)c * bin_cap + off] = i;
+        }
     }
 }
 
@@ -288,10 +311,13 @@ constexpr int kClusterCols = 64;       // at most 8 x 8 columns per cell
 // order within a cell differs from k_cell_sort's ascending input order.  The members
 // are counted per column and each is ranked only against its own column's keys.  The
 // order needs no particular rounding, only the same one every run, so the keys are
-// formed in FP32.
+// formed in FP32.  The members come from the cell's bin (bin_cap > 0) or from the
+// scatter (perm_tmp from cell_start); a cell whose members overflowed its bin gathers
+// them, in ascending input order, from the cell ids of all n atoms.
 template <bool BATCHED>
 __global__ void __launch_bounds__(kSortThreads)
 k_sort_cluster(const int *__restrict__ cell_start, const int *__restrict__ perm_tmp,
+               const int *__restrict__ bins, int bin_cap, const int *__restrict__ cell_id, int n,
                const float4 *__restrict__ pos_q, const int32_t *__restrict__ type, BoxF box_in,
                BatchArgs b, int32_t *__restrict__ perm, float4 *__restrict__ pos_q_sorted,
                int32_t *__restrict__ type_sorted)
@@ -300,24 +326,56 @@ k_sort_cluster(const int *__restrict__ cell_start, const int *__restrict__ perm_
     __shared__ unsigned long long s_bkt[kClusterSortMax];  // grouped by column
     __shared__ int s_col[kClusterCols + 1];                // counts, then column starts
     __shared__ int s_fill[kClusterCols];
+    __shared__ int s_wcnt[kSortThreads / 32];
     const int cg = blockIdx.x;
     const BoxF &box = BATCHED ? b.sys[b.cell_sys[cg]].box : box_in;
     const int c = BATCHED ? cg - b.sys[b.cell_sys[cg]].cell_offset : cg;
     const int s0 = cell_start[cg];
     const int m = cell_start[cg + 1] - s0;
     if (m == 0) return;
-    if (m > kClusterSortMax) {
+    const int *mem = bin_cap ? bins + (size_t)cg * bin_cap : perm_tmp + s0;
+    if (bin_cap && m > bin_cap) {
+        // ordered gather: members in ascending input order, placed directly when the
+        // cell is too large for the cluster order, else listed for it (in s_bkt)
+        int *list = reinterpret_cast<int *>(s_bkt);
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        int found = 0;
+        for (int base = 0; base < n; base += kSortThreads) {
+            const int j = base + threadIdx.x;
+            const bool mine = j < n && cell_id[j] == cg;
+            const unsigned bal = __ballot_sync(0xffffffffu, mine);
+            if (lane == 0) s_wcnt[warp] = __popc(bal);
+            __syncthreads();
+            int before = found, total = found;
+#pragma unroll
+            for (int w = 0; w < kSortThreads / 32; ++w) {
+                before += w < warp ? s_wcnt[w] : 0;
+                total += s_wcnt[w];
+            }
+            const int pos = before + __popc(bal & ((1u << lane) - 1u));
+            if (mine && pos < m) {
+                if (m > kClusterSortMax)
+                    place(j, s0 + pos, pos_q, type, box, perm, pos_q_sorted, type_sorted);
+                else
+                    list[pos] = j;
+            }
+            found = total;
+            __syncthreads();
+        }
+        if (m > kClusterSortMax) return;
+        mem = list;
+    } else if (m > kClusterSortMax) {
         // ascending input index, as k_cell_sort
         int *chunk = reinterpret_cast<int *>(s_key);
         constexpr int kChunk = 2 * kClusterSortMax;
         for (int base = 0; base < m; base += kSortThreads) {
             const int t = base + threadIdx.x;
-            const int e = t < m ? perm_tmp[s0 + t] : -1;
+            const int e = t < m ? mem[t] : -1;
             int rank = 0;
             for (int c0 = 0; c0 < m; c0 += kChunk) {
                 const int len = min(kChunk, m - c0);
                 __syncthreads();
-                for (int u = threadIdx.x; u < len; u += kSortThreads) chunk[u] = perm_tmp[s0 + c0 + u];
+                for (int u = threadIdx.x; u < len; u += kSortThreads) chunk[u] = mem[c0 + u];
                 __syncthreads();
                 for (int u = 0; u < len; ++u) rank += chunk[u] < e;
             }
@@ -336,7 +394,7 @@ k_sort_cluster(const int *__restrict__ cell_start, const int *__restrict__ perm_
     __syncthreads();
     const float fS = (float)S;
     for (int t = threadIdx.x; t < m; t += kSortThreads) {
-        const int e = perm_tmp[s0 + t];
+        const int e = mem[t];
         const float4 p = wrap_pos_f(pos_q[e], box);
         // position in cell units, clamped onto the cell's faces
         const float ux = __fsub_rn(__fmul_rn(p.x, box.inv_edge_f[0]), (float)cx);
@@ -426,6 +484,8 @@ cudaError_t launch_kick_drift_build(double *pos, double *vel, const void *forces
     int *perm_tmp = reinterpret_cast<int *>(wsp + ws.perm_tmp);
     void *accum = mode == MD_ACCUM_F64 ? nullptr : static_cast<void *>(wsp + ws.accum);
     int *work = reinterpret_cast<int *>(wsp + ws.work);
+    int *bins = reinterpret_cast<int *>(wsp + ws.bins);
+    const int cap = ws.bin_cap;
     const int ncell = b ? b->ncell : box_in.ncell;
     const BatchArgs nob = {};
     const BatchArgs &bb = b ? *b : nob;
@@ -437,22 +497,25 @@ cudaError_t launch_kick_drift_build(double *pos, double *vel, const void *forces
         const int g = (n + kStepThreads - 1) / kStepThreads;
         const int k = kick ? 1 : 0;
         if (b) {
-            if (sm) k_kick_drift_index<true, true><<<g, kStepThreads, sm, stream>>>(pos, vel, forces, mode, inv_mass, q, n, box_in, bb, dt, half_dt, k, pos_q, cell_id, cnt, cell_start, accum, work, status);
-            else k_kick_drift_index<false, true><<<g, kStepThreads, 0, stream>>>(pos, vel, forces, mode, inv_mass, q, n, box_in, bb, dt, half_dt, k, pos_q, cell_id, cnt, cell_start, accum, work, status);
+            if (sm) k_kick_drift_index<true, true><<<g, kStepThreads, sm, stream>>>(pos, vel, forces, mode, inv_mass, q, n, box_in, bb, dt, half_dt, k, pos_q, cell_id, cnt, cell_start, accum, work, bins, cap, status);
+            else k_kick_drift_index<false, true><<<g, kStepThreads, 0, stream>>>(pos, vel, forces, mode, inv_mass, q, n, box_in, bb, dt, half_dt, k, pos_q, cell_id, cnt, cell_start, accum, work, bins, cap, status);
         } else {
-            if (sm) k_kick_drift_index<true, false><<<g, kStepThreads, sm, stream>>>(pos, vel, forces, mode, inv_mass, q, n, box_in, bb, dt, half_dt, k, pos_q, cell_id, cnt, cell_start, accum, work, status);
-            else k_kick_drift_index<false, false><<<g, kStepThreads, 0, stream>>>(pos, vel, forces, mode, inv_mass, q, n, box_in, bb, dt, half_dt, k, pos_q, cell_id, cnt, cell_start, accum, work, status);
+            if (sm) k_kick_drift_index<true, false><<<g, kStepThreads, sm, stream>>>(pos, vel, forces, mode, inv_mass, q, n, box_in, bb, dt, half_dt, k, pos_q, cell_id, cnt, cell_start, accum, work, bins, cap, status);
+            else k_kick_drift_index<false, false><<<g, kStepThreads, 0, stream>>>(pos, vel, forces, mode, inv_mass, q, n, box_in, bb, dt, half_dt, k, pos_q, cell_id, cnt, cell_start, accum, work, bins, cap, status);
         }
     }
     // the shared-histogram form scans in its last block
     if (n == 0 || !sm) k_scan_cells<<<1, kScanThreads, 0, stream>>>(cnt, ncell, cell_start);
     if (n > 0) {
-        const int g = (n + kIndexThreads - 1) / kIndexThreads;
-        k_scatter<<<g, kIndexThreads, 0, stream>>>(cell_id, n, cnt, perm_tmp);
+        // with bins the members are already grouped by cell
+        if (!cap) {
+            const int g = (n + kIndexThreads - 1) / kIndexThreads;
+            k_scatter<<<g, kIndexThreads, 0, stream>>>(cell_id, n, cnt, perm_tmp);
+        }
         if (b)
-            k_sort_cluster<true><<<ncell, kSortThreads, 0, stream>>>(cell_start, perm_tmp, pos_q, type, box_in, bb, perm, pos_q_sorted, type_sorted);
+            k_sort_cluster<true><<<ncell, kSortThreads, 0, stream>>>(cell_start, perm_tmp, bins, cap, cell_id, n, pos_q, type, box_in, bb, perm, pos_q_sorted, type_sorted);
         else
-            k_sort_cluster<false><<<ncell, kSortThreads, 0, stream>>>(cell_start, perm_tmp, pos_q, type, box_in, bb, perm, pos_q_sorted, type_sorted);
+            k_sort_cluster<false><<<ncell, kSortThreads, 0, stream>>>(cell_start, perm_tmp, bins, cap, cell_id, n, pos_q, type, box_in, bb, perm, pos_q_sorted, type_sorted);
     }
     return cudaGetLastError();
 }

@@ -65,11 +65,16 @@ struct WsLayout {
     size_t st_cell_start, st_perm, st_pos_q_sorted, st_type_sorted, st_pos_q;  // md_step only
     size_t clu_pos_q, clu_type, clu_order;  // cluster-pair kernel: per-cell reordered copies
     size_t work;        // int[2] item counters of persistent force launches
+    size_t bins;        // int32 [ncell][bin_cap] members of each cell by arrival (MD step)
     size_t total;
     int nslots;
+    int bin_cap;        // 0: no bins (the step scatters through perm_tmp)
 };
 
-WsLayout ws_layout(int n, int ncell);
+// Members per cell that the MD step's bins hold: twice the mean occupancy plus 64,
+// rounded up to 32.  A cell with more members is gathered by a scan of the cell ids.
+int bin_capacity(int n, int ncell);
+WsLayout ws_layout(int n, int ncell, bool bins = true);
 
 // Layout of the batch workspace (byte offsets), derived on the host from the systems.
 struct BatchLayout {

@@ -134,17 +134,20 @@ def test_nve_energy_is_conserved_on_the_gentle_system(cuda_lib):
     assert abs(drifts[api.ACCUM_FIXED64] - drifts[api.ACCUM_F64]) < 0.05, drifts
 
 
-def test_step_cells_of_every_size(cuda_lib):
+@pytest.mark.parametrize("side", [11, 8])
+def test_step_cells_of_every_size(cuda_lib, side):
     """The MD step builds its cells straight in cluster order, with a separate path for
-    cells of more than 1,024 atoms. On a box that holds one such cell (1,331 atoms) and
-    cells of a few dozen, the start forces of md_step are the bits of md_nonbonded_forces
-    in FIXED64, and after one FIXED64 step the forces match the oracle at the new
+    cells of more than 1,024 atoms, and bins each cell's members up to twice the mean
+    occupancy plus 64 (a fuller cell is gathered from the cell ids). On a box that holds
+    one crowded cell (side^3 = 1,331 or 512 atoms, both past their bins) and cells of a
+    few dozen, the start forces of md_step are the bits of md_nonbonded_forces in
+    FIXED64, and after one FIXED64 step the forces match the oracle at the new
     positions."""
     from tests.test_gpu_parity import _custom
 
     api = cuda_lib
     rng = np.random.default_rng(11)
-    b = np.stack(np.meshgrid(*[np.arange(11)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    b = np.stack(np.meshgrid(*[np.arange(side)] * 3, indexing="ij"), -1).reshape(-1, 3)
     blob = 0.2 + 0.33 * b + rng.uniform(-0.02, 0.02, b.shape)
     rest = rng.uniform((5.5, 0.0, 0.0), (12.0, 12.0, 12.0), (300, 3))
     keep = np.ones(len(rest), bool)
