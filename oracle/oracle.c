@@ -381,7 +381,9 @@ double orc_kinetic_energy(int n, const double *vel, const double *inv_mass)
 /*
  * n_steps of kick-drift-kick velocity Verlet:
  *   v += dt/2 * a(x);  x += dt * v;  x <- wrap(x);  F = F(x);  v += dt/2 * a(x)
- * with a = F * inv_mass * 4.184e-4.  F holds F(x) on entry when f_valid is
+ * with a = F * inv_mass * 4.184e-4.  Each update is one correctly rounded fused
+ * multiply-add (C99 fma): v = fma(F, c, v) with c = dt/2 * inv_mass * 4.184e-4
+ * (evaluated left to right) and x = fma(dt, v, x).  F holds F(x) on entry when f_valid is
  * non-zero (else it is computed first) and F(x_final) on exit.  When
  * f32_positions is non-zero the forces are evaluated at the positions rounded
  * to float32 (the state itself stays float64).  energy_log (may be NULL) gets
@@ -406,15 +408,19 @@ int orc_vv_steps(int n, double *pos, double *vel, double *F, int f_valid,
     } while (0)
     if (!f_valid) ORC_FORCES();
     for (int s = 0; s < n_steps && rcode == 0; ++s) {
-        for (int i = 0; i < n; ++i)
+        for (int i = 0; i < n; ++i) {
+            const double kf = 0.5 * dt * inv_mass[i] * ORC_ACCEL;
             for (int c = 0; c < 3; ++c) {
-                vel[3 * i + c] += 0.5 * dt * F[3 * i + c] * inv_mass[i] * ORC_ACCEL;
-                pos[3 * i + c] = wrap_coord(pos[3 * i + c] + dt * vel[3 * i + c], L[c]);
+                vel[3 * i + c] = fma(F[3 * i + c], kf, vel[3 * i + c]);
+                pos[3 * i + c] = wrap_coord(fma(dt, vel[3 * i + c], pos[3 * i + c]), L[c]);
             }
+        }
         ORC_FORCES();
-        for (int i = 0; i < n; ++i)
+        for (int i = 0; i < n; ++i) {
+            const double kf = 0.5 * dt * inv_mass[i] * ORC_ACCEL;
             for (int c = 0; c < 3; ++c)
-                vel[3 * i + c] += 0.5 * dt * F[3 * i + c] * inv_mass[i] * ORC_ACCEL;
+                vel[3 * i + c] = fma(F[3 * i + c], kf, vel[3 * i + c]);
+        }
         if (energy_log) {
             energy_log[4 * s + 0] = en[0];
             energy_log[4 * s + 1] = en[1];

@@ -201,6 +201,7 @@ k_kick_drift_index(double *__restrict__ pos, double *__restrict__ vel, const voi
                    int *__restrict__ work, int *__restrict__ bins, int bin_cap, uint32_t *status)
 {
     extern __shared__ int s_hist[];
+    pdl_trigger();  // the cell sort may be scheduled now; it waits for this pass
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int ncell = BATCHED ? b.ncell : box_in.ncell;
     if (SMEM) {
@@ -226,10 +227,10 @@ k_kick_drift_index(double *__restrict__ pos, double *__restrict__ vel, const voi
         if (kick) {
             double f[3];
             load_force(forces, mode, i, f);
-            const double im = (double)inv_mass[i];
+            const double c = kick_factor((double)inv_mass[i], half_dt);
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                v[k] = kick_velocity(v[k], f[k], im, half_dt);
+                v[k] = kick_velocity(v[k], f[k], c);
                 vel[3 * i + k] = v[k];
             }
         }
@@ -327,6 +328,8 @@ k_sort_cluster(const int *__restrict__ cell_start, const int *__restrict__ perm_
     __shared__ int s_col[kClusterCols + 1];                // counts, then column starts
     __shared__ int s_fill[kClusterCols];
     __shared__ int s_wcnt[kSortThreads / 32];
+    pdl_wait();
+    pdl_trigger();
     const int cg = blockIdx.x;
     const BoxF &box = BATCHED ? b.sys[b.cell_sys[cg]].box : box_in;
     const int c = BATCHED ? cg - b.sys[b.cell_sys[cg]].cell_offset : cg;
@@ -512,10 +515,12 @@ cudaError_t launch_kick_drift_build(double *pos, double *vel, const void *forces
             const int g = (n + kIndexThreads - 1) / kIndexThreads;
             k_scatter<<<g, kIndexThreads, 0, stream>>>(cell_id, n, cnt, perm_tmp);
         }
+        // after the scatter, or straight after the build pass (programmatic launch)
         if (b)
-            k_sort_cluster<true><<<ncell, kSortThreads, 0, stream>>>(cell_start, perm_tmp, bins, cap, cell_id, n, pos_q, type, box_in, bb, perm, pos_q_sorted, type_sorted);
+            e = launch_pdl(k_sort_cluster<true>, dim3(ncell), dim3(kSortThreads), 0, stream, cell_start, perm_tmp, bins, cap, (const int *)cell_id, n, (const float4 *)pos_q, type, box_in, bb, perm, pos_q_sorted, type_sorted);
         else
-            k_sort_cluster<false><<<ncell, kSortThreads, 0, stream>>>(cell_start, perm_tmp, bins, cap, cell_id, n, pos_q, type, box_in, bb, perm, pos_q_sorted, type_sorted);
+            e = launch_pdl(k_sort_cluster<false>, dim3(ncell), dim3(kSortThreads), 0, stream, cell_start, perm_tmp, bins, cap, (const int *)cell_id, n, (const float4 *)pos_q, type, box_in, bb, perm, pos_q_sorted, type_sorted);
+        if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }

@@ -627,6 +627,8 @@ k_cluster(CluArgs a, BatchArgs bt, unsigned long long *sys_pair_count, int *work
     __shared__ __align__(16) CluSmem<MODE> sm;
     extern __shared__ __align__(16) unsigned char s_dyn[];
     float2 *s_ab = reinterpret_cast<float2 *>(s_dyn);  // LJ table [ntypes * ntypes]: (A, -B)
+    pdl_wait();
+    pdl_trigger();
     if (!PERSIST) {
         cluster_item<MODE, STATS, BATCHED, MI>(sm, s_ab, a, bt, sys_pair_count, blockIdx.x, blockIdx.y,
                                                gridDim.x);
@@ -655,6 +657,7 @@ k_finalize_clu(const void *__restrict__ accum, const int32_t *__restrict__ corde
                uint32_t *status, double *__restrict__ vel, const float *__restrict__ inv_mass,
                double half_dt)
 {
+    pdl_wait();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const int o = perm[corder ? corder[s] : s];
@@ -681,9 +684,9 @@ k_finalize_clu(const void *__restrict__ accum, const int32_t *__restrict__ corde
         f[2] = v.z;
     }
     if (KICK) {
-        const double im = (double)inv_mass[o];
+        const double c = kick_factor((double)inv_mass[o], half_dt);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) vel[3 * o + k] = kick_velocity(vel[3 * o + k], f[k], im, half_dt);
+        for (int k = 0; k < 3; ++k) vel[3 * o + k] = kick_velocity(vel[3 * o + k], f[k], c);
     }
 }
 
@@ -710,8 +713,8 @@ void launch_cluster_t(const CluArgs &c, dim3 grid, cudaStream_t stream, const Ba
         const long long items = (long long)grid.x * grid.y;
         g = dim3((unsigned)(items < wave ? items : wave), 1);
     }
-    k_cluster<MODE, STATS, BATCHED, MI, PERSIST><<<g, kCT, dyn, stream>>>(c, b, sys_pair_count, work,
-                                                                        (int)grid.x, (int)grid.y);
+    launch_pdl(k_cluster<MODE, STATS, BATCHED, MI, PERSIST>, g, dim3(kCT), dyn, stream, c, b,
+               sys_pair_count, work, (int)grid.x, (int)grid.y);
 }
 
 template <int MODE, bool MI>
@@ -820,17 +823,20 @@ cudaError_t launch_finalize_cluster(const ForceArgs &a, const void *accum, const
     const int32_t *corder = a.presorted ? nullptr : reinterpret_cast<const int32_t *>(wsp + ws.clu_order);
     const int g = (n + 255) / 256;
     const bool kick = a.kick_vel != nullptr;
+    const dim3 blk(256);
+    cudaError_t e;
     if (a.mode == MD_ACCUM_FIXED64) {
         if (kick)
-            k_finalize_clu<MD_ACCUM_FIXED64, true><<<g, 256, 0, stream>>>(accum, corder, a.perm, n, a.forces_out, a.status, a.kick_vel, a.kick_inv_mass, a.kick_half_dt);
+            e = launch_pdl(k_finalize_clu<MD_ACCUM_FIXED64, true>, dim3(g), blk, 0, stream, accum, corder, a.perm, n, a.forces_out, a.status, a.kick_vel, a.kick_inv_mass, a.kick_half_dt);
         else
-            k_finalize_clu<MD_ACCUM_FIXED64, false><<<g, 256, 0, stream>>>(accum, corder, a.perm, n, a.forces_out, a.status, nullptr, nullptr, 0.0);
+            e = launch_pdl(k_finalize_clu<MD_ACCUM_FIXED64, false>, dim3(g), blk, 0, stream, accum, corder, a.perm, n, a.forces_out, a.status, (double *)nullptr, (const float *)nullptr, 0.0);
     } else {
         if (kick)
-            k_finalize_clu<MD_ACCUM_F32, true><<<g, 256, 0, stream>>>(accum, corder, a.perm, n, a.forces_out, a.status, a.kick_vel, a.kick_inv_mass, a.kick_half_dt);
+            e = launch_pdl(k_finalize_clu<MD_ACCUM_F32, true>, dim3(g), blk, 0, stream, accum, corder, a.perm, n, a.forces_out, a.status, a.kick_vel, a.kick_inv_mass, a.kick_half_dt);
         else
-            k_finalize_clu<MD_ACCUM_F32, false><<<g, 256, 0, stream>>>(accum, corder, a.perm, n, a.forces_out, a.status, nullptr, nullptr, 0.0);
+            e = launch_pdl(k_finalize_clu<MD_ACCUM_F32, false>, dim3(g), blk, 0, stream, accum, corder, a.perm, n, a.forces_out, a.status, (double *)nullptr, (const float *)nullptr, 0.0);
     }
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "md_nonbonded.h"
 
 namespace mdnb {
@@ -88,6 +90,32 @@ struct BatchLayout {
     size_t total;
 };
 
+// ------------------------------------------------- programmatic dependent launch
+// The MD step's kernels after the first are launched with programmatic stream
+// serialization: such a kernel may be scheduled while its predecessor finishes, and
+// waits (pdl_wait) for the predecessor's completion and memory before it touches any
+// data that an earlier launch writes.  A kernel lets its dependent be scheduled
+// (pdl_trigger) once it has started.  Launched the ordinary way, both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t stream, Args &&...args)
+{
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // ----------------------------------------------------------------- device helpers
 
 __device__ __forceinline__ void set_status(uint32_t *status, uint32_t bits)
@@ -165,16 +193,21 @@ __device__ __forceinline__ int cell_of(const float4 &p, const BoxF &box, uint32_
     return cx + box.dims[0] * (cy + box.dims[1] * cz);
 }
 
-// Velocity-Verlet updates with every rounding spelled out (no contraction), in the
-// oracle's order: v + ((dt/2 F) (1/m)) 4.184e-4 and x + dt v.  Every kernel that moves
-// atoms uses these, so the single-system and batched steps agree bit for bit.
-__device__ __forceinline__ double kick_velocity(double v, double f, double im, double half_dt)
+// Velocity-Verlet updates with every rounding spelled out, in the oracle's order: the
+// per-atom factor c = ((dt/2) (1/m)) 4.184e-4, then v + F c and x + dt v each as one
+// fused multiply-add (one rounding).  Every kernel that moves atoms uses these, so the
+// single-system and batched steps agree bit for bit.
+__device__ __forceinline__ double kick_factor(double im, double half_dt)
 {
-    return __dadd_rn(v, __dmul_rn(__dmul_rn(__dmul_rn(half_dt, f), im), kAccelPerForcePerMass));
+    return __dmul_rn(__dmul_rn(half_dt, im), kAccelPerForcePerMass);
+}
+__device__ __forceinline__ double kick_velocity(double v, double f, double c)
+{
+    return __fma_rn(f, c, v);
 }
 __device__ __forceinline__ double drift_coord(double x, double v, double dt)
 {
-    return __dadd_rn(x, __dmul_rn(dt, v));
+    return __fma_rn(dt, v, x);
 }
 
 // A float position wrapped into the box by the FP64 rule and rounded back to float

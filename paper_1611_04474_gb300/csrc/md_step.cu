@@ -10,7 +10,7 @@ namespace {
 
 constexpr int kThreads = 256;
 
-// v += (dt/2) * F * inv_mass * 4.184e-4
+// v += F ((dt/2) inv_mass 4.184e-4)
 __global__ void __launch_bounds__(kThreads)
 k_kick(double *__restrict__ vel, const void *__restrict__ forces, int mode,
        const float *__restrict__ inv_mass, int n, double half_dt)
@@ -19,9 +19,9 @@ k_kick(double *__restrict__ vel, const void *__restrict__ forces, int mode,
     if (i >= n) return;
     double f[3];
     load_force(forces, mode, i, f);
-    double im = (double)inv_mass[i];
+    const double kf = kick_factor((double)inv_mass[i], half_dt);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) vel[3 * i + c] = kick_velocity(vel[3 * i + c], f[c], im, half_dt);
+    for (int c = 0; c < 3; ++c) vel[3 * i + c] = kick_velocity(vel[3 * i + c], f[c], kf);
 }
 
 // Per-block kinetic energy 1/2 m v^2 (kcal/mol) into partials[blockIdx.x].e_lj.
