@@ -186,9 +186,9 @@ __device__ __forceinline__ void block_scan_cells(int *__restrict__ cnt_cursor, i
 // from its system, cells numbered over the batch.  It also zeroes the force kernels'
 // cluster-order accumulators (`accum`, MD_ACCUM_F32 float4[n] or MD_ACCUM_FIXED64
 // u64[3][n]; null for none) and the persistent launches' item counters (`work`, may be
-// null).  SMEM (ncell <= kStepSmemCells): the last block to finish also scans the
-// histogram into cell_start and the scatter cursors; cell_cnt[ncell] counts finished
-// blocks and must be zero at launch.  bin_cap > 0: each atom also takes a slot of its
+// null).  SMEM (ncell <= kStepSmemCells) without bins: the last block to finish also
+// scans the histogram into cell_start and the scatter cursors; cell_cnt[ncell] counts
+// finished blocks and must be zero at launch.  bin_cap > 0: each atom also takes a slot of its
 // cell's bin (bins[c][0..bin_cap), by arrival; the count atomics hand out the slots),
 // which replaces the scatter pass; members past bin_cap are not binned.
 template <bool SMEM, bool BATCHED>
@@ -280,16 +280,19 @@ k_kick_drift_index(double *__restrict__ pos, double *__restrict__ vel, const voi
                 if (off < bin_cap) bins[(size_t)c * bin_cap + off] = i;
             }
         }
-        // the last block to finish scans the counts (each block's adds are made visible
-        // before it is counted)
-        __shared__ int s_last;
-        __threadfence();
-        __syncthreads();
-        if (threadIdx.x == 0) s_last = atomicAdd(&cell_cnt[ncell], 1) == (int)gridDim.x - 1;
-        __syncthreads();
-        if (s_last) {
+        // without bins the last block to finish scans the counts for the scatter (each
+        // block's adds are made visible before it is counted); with bins the cell sort
+        // forms each cell's start itself
+        if (!bin_cap) {
+            __shared__ int s_last;
             __threadfence();
-            block_scan_cells(cell_cnt, ncell, cell_start, s_hist);
+            __syncthreads();
+            if (threadIdx.x == 0) s_last = atomicAdd(&cell_cnt[ncell], 1) == (int)gridDim.x - 1;
+            __syncthreads();
+            if (s_last) {
+                __threadfence();
+                block_scan_cells(cell_cnt, ncell, cell_start, s_hist);
+            }
         }
     } else {
         int base = 0;
@@ -314,11 +317,13 @@ constexpr int kClusterCols = 64;       // at most 8 x 8 columns per cell
 // order needs no particular rounding, only the same one every run, so the keys are
 // formed in FP32.  The members come from the cell's bin (bin_cap > 0) or from the
 // scatter (perm_tmp from cell_start); a cell whose members overflowed its bin gathers
-// them, in ascending input order, from the cell ids of all n atoms.
+// them, in ascending input order, from the cell ids of all n atoms.  counts (non-null,
+// with bins): cell_start is formed here from the per-cell counts of all ncell cells.
 template <bool BATCHED>
 __global__ void __launch_bounds__(kSortThreads)
-k_sort_cluster(const int *__restrict__ cell_start, const int *__restrict__ perm_tmp,
+k_sort_cluster(int *__restrict__ cell_start, const int *__restrict__ perm_tmp,
                const int *__restrict__ bins, int bin_cap, const int *__restrict__ cell_id, int n,
+               const int *__restrict__ counts, int ncell,
                const float4 *__restrict__ pos_q, const int32_t *__restrict__ type, BoxF box_in,
                BatchArgs b, int32_t *__restrict__ perm, float4 *__restrict__ pos_q_sorted,
                int32_t *__restrict__ type_sorted)
@@ -333,8 +338,29 @@ k_sort_cluster(const int *__restrict__ cell_start, const int *__restrict__ perm_
     const int cg = blockIdx.x;
     const BoxF &box = BATCHED ? b.sys[b.cell_sys[cg]].box : box_in;
     const int c = BATCHED ? cg - b.sys[b.cell_sys[cg]].cell_offset : cg;
-    const int s0 = cell_start[cg];
-    const int m = cell_start[cg + 1] - s0;
+    int s0, m;
+    if (counts) {
+        // this cell's start from the counts of the cells before it (a block sum), and
+        // cell_start written here
+        int part = 0;
+        for (int t = threadIdx.x; t < cg; t += kSortThreads) part += __ldcg(counts + t);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if ((threadIdx.x & 31) == 0) s_wcnt[threadIdx.x >> 5] = part;
+        __syncthreads();
+        s0 = 0;
+#pragma unroll
+        for (int w = 0; w < kSortThreads / 32; ++w) s0 += s_wcnt[w];
+        m = __ldcg(counts + cg);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            cell_start[cg] = s0;
+            if (cg == ncell - 1) cell_start[ncell] = s0 + m;
+        }
+    } else {
+        s0 = cell_start[cg];
+        m = cell_start[cg + 1] - s0;
+    }
     if (m == 0) return;
     const int *mem = bin_cap ? bins + (size_t)cg * bin_cap : perm_tmp + s0;
     if (bin_cap && m > bin_cap) {
@@ -507,7 +533,9 @@ cudaError_t launch_kick_drift_build(double *pos, double *vel, const void *forces
             else k_kick_drift_index<false, false><<<g, kStepThreads, 0, stream>>>(pos, vel, forces, mode, inv_mass, q, n, box_in, bb, dt, half_dt, k, pos_q, cell_id, cnt, cell_start, accum, work, bins, cap, status);
         }
     }
-    // the shared-histogram form scans in its last block
+    // the shared-histogram form scans in its last block (without bins) or in the cell
+    // sort (with bins)
+    const bool sort_scans = n > 0 && sm && cap;
     if (n == 0 || !sm) k_scan_cells<<<1, kScanThreads, 0, stream>>>(cnt, ncell, cell_start);
     if (n > 0) {
         // with bins the members are already grouped by cell
@@ -517,9 +545,9 @@ cudaError_t launch_kick_drift_build(double *pos, double *vel, const void *forces
         }
         // after the scatter, or straight after the build pass (programmatic launch)
         if (b)
-            e = launch_pdl(k_sort_cluster<true>, dim3(ncell), dim3(kSortThreads), 0, stream, cell_start, perm_tmp, bins, cap, (const int *)cell_id, n, (const float4 *)pos_q, type, box_in, bb, perm, pos_q_sorted, type_sorted);
+            e = launch_pdl(k_sort_cluster<true>, dim3(ncell), dim3(kSortThreads), 0, stream, cell_start, perm_tmp, bins, cap, (const int *)cell_id, n, sort_scans ? (const int *)cnt : nullptr, ncell, (const float4 *)pos_q, type, box_in, bb, perm, pos_q_sorted, type_sorted);
         else
-            e = launch_pdl(k_sort_cluster<false>, dim3(ncell), dim3(kSortThreads), 0, stream, cell_start, perm_tmp, bins, cap, (const int *)cell_id, n, (const float4 *)pos_q, type, box_in, bb, perm, pos_q_sorted, type_sorted);
+            e = launch_pdl(k_sort_cluster<false>, dim3(ncell), dim3(kSortThreads), 0, stream, cell_start, perm_tmp, bins, cap, (const int *)cell_id, n, sort_scans ? (const int *)cnt : nullptr, ncell, (const float4 *)pos_q, type, box_in, bb, perm, pos_q_sorted, type_sorted);
         if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
