@@ -333,6 +333,8 @@ k_sort_cluster(int *__restrict__ cell_start, const int *__restrict__ perm_tmp,
     __shared__ int s_col[kClusterCols + 1];                // counts, then column starts
     __shared__ int s_fill[kClusterCols];
     __shared__ int s_wcnt[kSortThreads / 32];
+    __shared__ float4 s_pos[kClusterSortMax];  // wrapped positions + charges, by arrival
+    __shared__ int s_typ[kClusterSortMax];     // types, by arrival
     pdl_wait();
     pdl_trigger();
     const int cg = blockIdx.x;
@@ -342,6 +344,7 @@ k_sort_cluster(int *__restrict__ cell_start, const int *__restrict__ perm_tmp,
     if (counts) {
         // this cell's start from the counts of the cells before it (a block sum), and
         // cell_start written here
+        m = __ldcg(counts + cg);
         int part = 0;
         for (int t = threadIdx.x; t < cg; t += kSortThreads) part += __ldcg(counts + t);
 #pragma unroll
@@ -351,7 +354,6 @@ k_sort_cluster(int *__restrict__ cell_start, const int *__restrict__ perm_tmp,
         s0 = 0;
 #pragma unroll
         for (int w = 0; w < kSortThreads / 32; ++w) s0 += s_wcnt[w];
-        m = __ldcg(counts + cg);
         __syncthreads();
         if (threadIdx.x == 0) {
             cell_start[cg] = s0;
@@ -425,6 +427,8 @@ k_sort_cluster(int *__restrict__ cell_start, const int *__restrict__ perm_tmp,
     for (int t = threadIdx.x; t < m; t += kSortThreads) {
         const int e = mem[t];
         const float4 p = wrap_pos_f(pos_q[e], box);
+        s_pos[t] = p;
+        s_typ[t] = type[e];
         // position in cell units, clamped onto the cell's faces
         const float ux = __fsub_rn(__fmul_rn(p.x, box.inv_edge_f[0]), (float)cx);
         const float uy = __fsub_rn(__fmul_rn(p.y, box.inv_edge_f[1]), (float)cy);
@@ -462,8 +466,11 @@ k_sort_cluster(int *__restrict__ cell_start, const int *__restrict__ perm_tmp,
         const int b0 = s_col[col], b1 = s_col[col + 1];
         int rank = 0;
         for (int u = b0; u < b1; ++u) rank += s_bkt[u] < key;
-        place((int)(key & ((1ull << 30) - 1)), s0 + b0 + rank, pos_q, type, box, perm, pos_q_sorted,
-              type_sorted);
+        // what place() writes, from the copies staged above
+        const int slot = s0 + b0 + rank;
+        perm[slot] = (int)(key & ((1ull << 30) - 1));
+        pos_q_sorted[slot] = s_pos[t];
+        type_sorted[slot] = s_typ[t];
     }
 }
 
