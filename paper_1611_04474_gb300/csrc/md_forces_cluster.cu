@@ -178,7 +178,10 @@ struct CluSmem {
     float ib[6][kCTile / kCS];  // home cluster boxes: lo xyz, hi xyz (one row per bound)
     float jb[6][kCTile / kCS];  // neighbour cluster boxes
     Acc hf[3][kCTile];          // forces on home atoms (whole cell pair)
-    Acc nf[NW][3][kCTile];      // reactions on neighbour atoms (this tile)
+    // reactions on neighbour atoms (this tile), component d of atom t at d * kRow + t
+    static constexpr int kRow = kCTile;
+    Acc nf[NW][2 * kRow + kCTile];
+    __device__ __forceinline__ Acc &react(int w, int d, int t) { return nf[w][d * kRow + t]; }
     int next;                   // next home cluster to hand out
 };
 
@@ -356,17 +359,16 @@ __device__ __forceinline__ void cluster_row(CluSmem<MODE> &sm, const float2 *s_a
                 vy += __shfl_xor_sync(0xffffffffu, vy, o);
                 vz += __shfl_xor_sync(0xffffffffu, vz, o);
             }
-            if (il == 0) {
-                if (MODE == MD_ACCUM_FIXED64) {
-                    atomicAdd(reinterpret_cast<unsigned long long *>(&sm.nf[0][0][ja]), (unsigned long long)(Acc(0) - vx));
-                    atomicAdd(reinterpret_cast<unsigned long long *>(&sm.nf[0][1][ja]), (unsigned long long)(Acc(0) - vy));
-                    atomicAdd(reinterpret_cast<unsigned long long *>(&sm.nf[0][2][ja]), (unsigned long long)(Acc(0) - vz));
-                } else {
-                    Acc(*nf)[kCTile] = sm.nf[MODE == MD_ACCUM_FIXED64 ? 0 : warp];
-                    nf[0][ja] -= vx;
-                    nf[1][ja] -= vy;
-                    nf[2][ja] -= vz;
+            if (MODE == MD_ACCUM_FIXED64) {
+                // the butterfly left the sums in all 4 lanes of ja: lane il adds component il
+                if (il < 3) {
+                    const Acc v = il == 0 ? vx : (il == 1 ? vy : vz);
+                    atomicAdd(reinterpret_cast<unsigned long long *>(&sm.react(0, il, ja)), (unsigned long long)(Acc(0) - v));
                 }
+            } else if (il == 0) {
+                sm.react(warp, 0, ja) -= vx;
+                sm.react(warp, 1, ja) -= vy;
+                sm.react(warp, 2, ja) -= vz;
             }
         }
     }
@@ -540,7 +542,7 @@ __device__ __forceinline__ void cluster_item(CluSmem<MODE> &sm, float2 *s_ab, co
                 sm.np[t] = p;
                 sm.nt[t] = ty;
 #pragma unroll
-                for (int w = 0; w < CluSmem<MODE>::NW; ++w) sm.nf[w][0][t] = sm.nf[w][1][t] = sm.nf[w][2][t] = Acc(0);
+                for (int w = 0; w < CluSmem<MODE>::NW; ++w) sm.react(w, 0, t) = sm.react(w, 1, t) = sm.react(w, 2, t) = Acc(0);
             }
             __syncthreads();
             cluster_boxes(sm.np, mn, sm.jb);
@@ -560,12 +562,12 @@ __device__ __forceinline__ void cluster_item(CluSmem<MODE> &sm, float2 *s_ab, co
             }
             __syncthreads();
             for (int t = threadIdx.x; t < mn; t += kCT) {
-                Acc sx = sm.nf[0][0][t], sy = sm.nf[0][1][t], sz = sm.nf[0][2][t];
+                Acc sx = sm.react(0, 0, t), sy = sm.react(0, 1, t), sz = sm.react(0, 2, t);
 #pragma unroll
                 for (int w = 1; w < CluSmem<MODE>::NW; ++w) {
-                    sx += sm.nf[w][0][t];
-                    sy += sm.nf[w][1][t];
-                    sz += sm.nf[w][2][t];
+                    sx += sm.react(w, 0, t);
+                    sy += sm.react(w, 1, t);
+                    sz += sm.react(w, 2, t);
                 }
                 if (diag) {
                     // the neighbour tile is the home tile: reactions join the home sums
