@@ -397,34 +397,32 @@ def run_ours(args):
     energy = None if args.no_energy else measure_energy(eng, stream, dev.index)
 
     # end to end through the public API with host buffers: the step's state (positions,
-    # velocities, forces) and its energy row live in one pinned host buffer and one device
-    # buffer, so that each step is one copy in and one copy out around md_step
+    # velocities, forces) lives in one pinned host buffer and one device buffer, so that
+    # each step is one copy in, the same md_step as the device-timed steps, and one copy
+    # of the new state out
     n = s.n
-    sizes = [n * 3 * 8, n * 3 * 8, n * 3 * eng.forces.element_size(), 4 * 8]
+    sizes = [n * 3 * 8, n * 3 * 8, n * 3 * eng.forces.element_size()]
     offs = [0]
     for b in sizes:
         offs.append(offs[-1] + ((b + 255) // 256) * 256)
     dev_buf = torch.empty(offs[-1], dtype=torch.uint8, device=dev)
-    views = [dev_buf[offs[k]:offs[k] + sizes[k]] for k in range(4)]
+    views = [dev_buf[offs[k]:offs[k] + sizes[k]] for k in range(3)]
     pos_d = views[0].view(torch.float64).view(n, 3)
     vel_d = views[1].view(torch.float64).view(n, 3)
     F_d = views[2].view(eng.forces.dtype).view(n, 3)
-    elog = views[3].view(torch.float64).view(1, 4)
     pos_d.copy_(eng.pos)
     vel_d.copy_(eng.vel)
     F_d.copy_(eng.forces)
     eng.pos, eng.vel, eng.forces = pos_d, vel_d, F_d
     host_buf = dev_buf.cpu().pin_memory()
-    state_bytes = offs[3]  # positions, velocities, forces
-    h2d = state_bytes
-    d2h = offs[-1]
+    h2d = d2h = offs[-1]
     e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)]
     for k in range(args.steps):
         flush.fill_(k & 0xFF)
         e2e_ev[k][0].record(stream)
-        dev_buf[:state_bytes].copy_(host_buf[:state_bytes], non_blocking=True)
-        eng.step(1, dt_fs=args.dt, energy_log=elog)
+        dev_buf.copy_(host_buf, non_blocking=True)
+        eng.step(1, dt_fs=args.dt)
         host_buf.copy_(dev_buf, non_blocking=True)
         e2e_ev[k][1].record(stream)
     torch.cuda.synchronize()
