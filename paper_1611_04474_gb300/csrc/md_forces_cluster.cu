@@ -178,8 +178,10 @@ struct CluSmem {
     float ib[6][kCTile / kCS];  // home cluster boxes: lo xyz, hi xyz (one row per bound)
     float jb[6][kCTile / kCS];  // neighbour cluster boxes
     Acc hf[3][kCTile];          // forces on home atoms (whole cell pair)
-    // reactions on neighbour atoms (this tile), component d of atom t at d * kRow + t
-    static constexpr int kRow = kCTile;
+    // reactions on neighbour atoms (this tile), component d of atom t at d * kRow + t;
+    // F32 rows are 8 words longer, so that the three lanes that add the x, y and z of
+    // one atom hit different banks
+    static constexpr int kRow = kCTile + (MODE == MD_ACCUM_FIXED64 ? 0 : 8);
     Acc nf[NW][2 * kRow + kCTile];
     __device__ __forceinline__ Acc &react(int w, int d, int t) { return nf[w][d * kRow + t]; }
     int next;                   // next home cluster to hand out
@@ -353,44 +355,29 @@ __device__ __forceinline__ void cluster_row(CluSmem<MODE> &sm, const float2 *s_a
                     vir += f1 * r21;
                 }
             }
-#pragma unroll
-            for (int o = 1; o < 4; o <<= 1) {
-                vx += __shfl_xor_sync(0xffffffffu, vx, o);
-                vy += __shfl_xor_sync(0xffffffffu, vy, o);
-                vz += __shfl_xor_sync(0xffffffffu, vz, o);
-            }
-            if (MODE == MD_ACCUM_FIXED64) {
-                // the butterfly left the sums in all 4 lanes of ja: lane il adds component il
+            {
+                // reduce-scatter of (x, y, z, 0) over the 4 lanes of ja (3 shuffles instead
+                // of the 6 of a butterfly): the lanes with il & 2 keep (z, 0), the others
+                // (x, y); then il & 1 picks one of the two.  Lane il ends with component il.
+                const bool hi2 = (il & 2) != 0, hi1 = (il & 1) != 0;
+                const Acc s0 = hi2 ? vx : vz, s1 = hi2 ? vy : Acc(0);
+                const Acc k0 = (hi2 ? vz : vx) + __shfl_xor_sync(0xffffffffu, s0, 2);
+                const Acc k1 = (hi2 ? Acc(0) : vy) + __shfl_xor_sync(0xffffffffu, s1, 2);
+                const Acc t = (hi1 ? k1 : k0) + __shfl_xor_sync(0xffffffffu, hi1 ? k0 : k1, 1);
                 if (il < 3) {
-                    const Acc v = il == 0 ? vx : (il == 1 ? vy : vz);
-                    atomicAdd(reinterpret_cast<unsigned long long *>(&sm.react(0, il, ja)), (unsigned long long)(Acc(0) - v));
+                    if (MODE == MD_ACCUM_FIXED64)
+                        atomicAdd(reinterpret_cast<unsigned long long *>(&sm.react(0, il, ja)), (unsigned long long)(Acc(0) - t));
+                    else
+                        sm.react(warp, il, ja) -= t;
                 }
-            } else if (il == 0) {
-                sm.react(warp, 0, ja) -= vx;
-                sm.react(warp, 1, ja) -= vy;
-                sm.react(warp, 2, ja) -= vz;
             }
         }
     }
-    // home-atom sums over the 8 lanes that share them; the home cluster belongs to
-    // this warp alone within the CTA
-    if (MODE == MD_ACCUM_FIXED64) {
-#pragma unroll
-        for (int o = 4; o < 32; o <<= 1) {
-            ax0 += __shfl_xor_sync(0xffffffffu, ax0, o);
-            ay0 += __shfl_xor_sync(0xffffffffu, ay0, o);
-            az0 += __shfl_xor_sync(0xffffffffu, az0, o);
-            ax1 += __shfl_xor_sync(0xffffffffu, ax1, o);
-            ay1 += __shfl_xor_sync(0xffffffffu, ay1, o);
-            az1 += __shfl_xor_sync(0xffffffffu, az1, o);
-        }
-    } else {
-#pragma unroll
-        for (int o = 4; o < 32; o <<= 1) {
-            ax2 = f2_add(ax2, __shfl_xor_sync(0xffffffffu, ax2, o));
-            ay2 = f2_add(ay2, __shfl_xor_sync(0xffffffffu, ay2, o));
-            az2 = f2_add(az2, __shfl_xor_sync(0xffffffffu, az2, o));
-        }
+    // home-atom sums over the 8 lanes that share them (the home cluster belongs to this
+    // warp alone within the CTA): a reduce-scatter of the six (atom, component) sums over
+    // the lane bits of jl, after which lane jl < 6 holds sum jl (atom ia0 for jl < 3,
+    // ia1 above, component jl % 3) and adds it to the home tile
+    if (MODE != MD_ACCUM_FIXED64) {
         float a, b;
         f2_split(ax2, a, b);
         ax0 = (Acc)a;
@@ -402,17 +389,20 @@ __device__ __forceinline__ void cluster_row(CluSmem<MODE> &sm, const float2 *s_a
         az0 = (Acc)a;
         az1 = (Acc)b;
     }
-    if (jl == 0) {
-        if (ia0 < mh) {
-            sm.hf[0][ia0] += ax0;
-            sm.hf[1][ia0] += ay0;
-            sm.hf[2][ia0] += az0;
+    Acc w[8] = {ax0, ay0, az0, ax1, ay1, az1, Acc(0), Acc(0)};
+#pragma unroll
+    for (int half = 4, o = 16; half >= 1; half >>= 1, o >>= 1) {
+        const bool up = (lane & o) != 0;  // keep the upper half of the current values
+#pragma unroll
+        for (int q = 0; q < half; ++q) {
+            const Acc send = up ? w[q] : w[q + half];
+            const Acc keep = up ? w[q + half] : w[q];
+            w[q] = keep + __shfl_xor_sync(0xffffffffu, send, o);
         }
-        if (ia1 < mh) {
-            sm.hf[0][ia1] += ax1;
-            sm.hf[1][ia1] += ay1;
-            sm.hf[2][ia1] += az1;
-        }
+    }
+    if (jl < 6) {
+        const int ia = jl < 3 ? ia0 : ia1;
+        if (ia < mh) sm.hf[jl < 3 ? jl : jl - 3][ia] += w[0];
     }
 }
 
