@@ -47,6 +47,7 @@ constexpr int kCT = kCW * 32;   // threads per CTA
 constexpr int kCTile = 256;     // atoms of a cell staged at once (whole clusters)
 constexpr int kSortMax = 1024;  // cells with more atoms keep their sorted order
 constexpr int kOrderThreads = 256;
+constexpr int kOrderCols = 64;   // at most 8 x 8 columns per cell
 
 static_assert(kCTile % kCS == 0 && kCTile / kCS <= 32, "a tile's clusters fit one ballot");
 
@@ -56,14 +57,19 @@ constexpr int kStatsNone = 0;    // forces only
 constexpr int kStatsCount = 1;   // + within-cutoff pair count
 constexpr int kStatsEnergy = 2;  // + count, energies and virial
 // Per cell: sort its atoms by (column, z along the column) and write the reordered
-// copies.  corder[k] is the sorted-order slot of cluster-order slot k.  (The MD steps
+// copies.  corder[k] is the sorted-order slot of cluster-order slot k.  The members are
+// counted per column and each is ranked only against its own column's keys.  (The MD steps
 // build their cells in this order directly: k_sort_cluster.)
 __global__ void __launch_bounds__(kOrderThreads)
 k_cluster_order(const int32_t *__restrict__ cell_start, const float4 *__restrict__ pq,
                 const int32_t *__restrict__ ty, BoxF box, float4 *__restrict__ cpq,
                 int32_t *__restrict__ cty, int32_t *__restrict__ corder)
 {
-    __shared__ unsigned long long s_key[kSortMax];
+    __shared__ unsigned long long s_key[kSortMax];  // by sorted slot
+    __shared__ unsigned long long s_bkt[kSortMax];  // grouped by column
+    __shared__ int s_col[kOrderCols + 1];           // counts, then column starts
+    __shared__ int s_fill[kOrderCols];
+    pdl_trigger();  // the force kernel may be scheduled now; it waits for this pass
     const int cg = blockIdx.x, c = cg;
     const int b = cell_start[cg], m = cell_start[cg + 1] - b;
     if (m <= 0) return;
@@ -79,6 +85,12 @@ k_cluster_order(const int32_t *__restrict__ cell_start, const float4 *__restrict
     const int cx = c % nx, cy = (c / nx) % ny, cz = c / (nx * ny);
     // about 20 atoms per column
     const int S = max(1, min(8, (int)(sqrtf((float)m * (1.0f / 20.0f)) + 0.5f)));
+    const int ncol = S * S;
+    for (int t = threadIdx.x; t < ncol; t += kOrderThreads) {
+        s_col[t] = 0;
+        s_fill[t] = 0;
+    }
+    __syncthreads();
     const float ex = (float)box.inv_edge[0], ey = (float)box.inv_edge[1], ez = (float)box.inv_edge[2];
     for (int t = threadIdx.x; t < m; t += kOrderThreads) {
         const float4 p = pq[b + t];
@@ -91,12 +103,32 @@ k_cluster_order(const int32_t *__restrict__ cell_start, const float4 *__restrict
         const unsigned zq = (unsigned)(uz * 1048575.0f);
         s_key[t] = ((unsigned long long)col << 44) | ((unsigned long long)zq << 20) |
                    (unsigned long long)t;
+        atomicAdd(&s_col[col], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int k = 0; k < ncol; ++k) {
+            const int v = s_col[k];
+            s_col[k] = run;
+            run += v;
+        }
+        s_col[ncol] = run;
     }
     __syncthreads();
     for (int t = threadIdx.x; t < m; t += kOrderThreads) {
         const unsigned long long k = s_key[t];
-        int rank = 0;
-        for (int u = 0; u < m; ++u) rank += s_key[u] < k;
+        const int col = (int)(k >> 44);
+        s_bkt[s_col[col] + atomicAdd(&s_fill[col], 1)] = k;
+    }
+    __syncthreads();
+    // each member ranked against its own column only
+    for (int t = threadIdx.x; t < m; t += kOrderThreads) {
+        const unsigned long long k = s_key[t];
+        const int col = (int)(k >> 44);
+        const int b0 = s_col[col], b1 = s_col[col + 1];
+        int rank = b0;
+        for (int u = b0; u < b1; ++u) rank += s_bkt[u] < k;
         corder[b + rank] = b + t;
         cpq[b + rank] = pq[b + t];
         cty[b + rank] = ty[b + t];
