@@ -63,7 +63,8 @@ constexpr int kStatsEnergy = 2;  // + count, energies and virial
 __global__ void __launch_bounds__(kOrderThreads)
 k_cluster_order(const int32_t *__restrict__ cell_start, const float4 *__restrict__ pq,
                 const int32_t *__restrict__ ty, BoxF box, float4 *__restrict__ cpq,
-                int32_t *__restrict__ cty, int32_t *__restrict__ corder)
+                int32_t *__restrict__ cty, int32_t *__restrict__ corder, void *__restrict__ accum,
+                int mode, int n)
 {
     __shared__ unsigned long long s_key[kSortMax];  // by sorted slot
     __shared__ unsigned long long s_bkt[kSortMax];  // grouped by column
@@ -73,6 +74,17 @@ k_cluster_order(const int32_t *__restrict__ cell_start, const float4 *__restrict
     const int cg = blockIdx.x, c = cg;
     const int b = cell_start[cg], m = cell_start[cg + 1] - b;
     if (m <= 0) return;
+    // the force kernel's accumulators of this cell's slots start at zero
+    for (int t = threadIdx.x; t < m; t += kOrderThreads) {
+        if (mode == MD_ACCUM_FIXED64) {
+            unsigned long long *A = static_cast<unsigned long long *>(accum);
+            A[b + t] = 0ull;
+            A[(size_t)n + b + t] = 0ull;
+            A[2 * (size_t)n + b + t] = 0ull;
+        } else {
+            static_cast<float4 *>(accum)[b + t] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        }
+    }
     if (m > kSortMax) {
         for (int t = threadIdx.x; t < m; t += kOrderThreads) {
             corder[b + t] = b + t;
@@ -759,11 +771,14 @@ cudaError_t launch_cluster(const ForceArgs &a, const WsLayout &ws, char *wsp, Pa
     float4 *cpq = reinterpret_cast<float4 *>(wsp + ws.clu_pos_q);
     int32_t *cty = reinterpret_cast<int32_t *>(wsp + ws.clu_type);
     int32_t *corder = reinterpret_cast<int32_t *>(wsp + ws.clu_order);
-    cudaError_t e = a.accum_zeroed ? cudaSuccess : cudaMemsetAsync(accum, 0, acc_bytes, stream);
+    // the MD step's build pass, or else the ordering pass, zeroes the accumulators; a
+    // presorted call without that needs the memset
+    cudaError_t e = a.accum_zeroed || !a.presorted ? cudaSuccess : cudaMemsetAsync(accum, 0, acc_bytes, stream);
     if (e != cudaSuccess) return e;
     if (!a.presorted)
         k_cluster_order<<<a.box.ncell, kOrderThreads, 0, stream>>>(a.cell_start, a.pos_q_sorted,
-                                                                   a.type_sorted, a.box, cpq, cty, corder);
+                                                                   a.type_sorted, a.box, cpq, cty, corder,
+                                                                   accum, a.mode, a.n);
     CluArgs c;
     c.cell_start = a.cell_start;
     c.pq = a.presorted ? a.pos_q_sorted : cpq;
