@@ -8,6 +8,11 @@
 //   4. k_cell_sort  : one block per cell ranks its members by input index, which
 //                     restores a deterministic order, and gathers the wrapped
 //                     float4 positions and types into sorted order.
+//
+// The MD step fuses this with its integration (k_kick_drift_index: half kick, drift,
+// wrap, cell index, count and a slot in a per-cell bin) and builds each cell straight
+// in the force kernel's cluster order (k_sort_cluster), without the scan and the
+// scatter when the bins hold every cell.
 #include "md_internal.cuh"
 
 namespace mdnb {
