@@ -729,8 +729,9 @@ k_finalize_clu(const void *__restrict__ accum, const int32_t *__restrict__ corde
 // grid: cells x stencil entries.  PERSIST: the same items from about one wave of CTAs
 // (blocks per SM at this launch's shared memory x SMs), taking items from `work`.
 template <int MODE, int STATS, bool BATCHED = false, bool MI = false, bool PERSIST = false>
-void launch_cluster_t(const CluArgs &c, dim3 grid, cudaStream_t stream, const BatchArgs &b = BatchArgs{},
-                      unsigned long long *sys_pair_count = nullptr, int *work = nullptr)
+cudaError_t launch_cluster_t(const CluArgs &c, dim3 grid, cudaStream_t stream,
+                             const BatchArgs &b = BatchArgs{},
+                             unsigned long long *sys_pair_count = nullptr, int *work = nullptr)
 {
     const size_t dyn = sizeof(float2) * (size_t)c.ntypes * (size_t)c.ntypes;
     static const cudaError_t attr = cudaFuncSetAttribute(
@@ -749,16 +750,16 @@ void launch_cluster_t(const CluArgs &c, dim3 grid, cudaStream_t stream, const Ba
         const long long items = (long long)grid.x * grid.y;
         g = dim3((unsigned)(items < wave ? items : wave), 1);
     }
-    launch_pdl(k_cluster<MODE, STATS, BATCHED, MI, PERSIST>, g, dim3(kCT), dyn, stream, c, b,
-               sys_pair_count, work, (int)grid.x, (int)grid.y);
+    return launch_pdl(k_cluster<MODE, STATS, BATCHED, MI, PERSIST>, g, dim3(kCT), dyn, stream, c, b,
+                      sys_pair_count, work, (int)grid.x, (int)grid.y);
 }
 
 template <int MODE, bool MI>
-void launch_cluster_stats(int stats, const CluArgs &c, dim3 grid, cudaStream_t stream)
+cudaError_t launch_cluster_stats(int stats, const CluArgs &c, dim3 grid, cudaStream_t stream)
 {
-    if (stats == kStatsEnergy) launch_cluster_t<MODE, kStatsEnergy, false, MI>(c, grid, stream);
-    else if (stats == kStatsCount) launch_cluster_t<MODE, kStatsCount, false, MI>(c, grid, stream);
-    else launch_cluster_t<MODE, kStatsNone, false, MI>(c, grid, stream);
+    if (stats == kStatsEnergy) return launch_cluster_t<MODE, kStatsEnergy, false, MI>(c, grid, stream);
+    if (stats == kStatsCount) return launch_cluster_t<MODE, kStatsCount, false, MI>(c, grid, stream);
+    return launch_cluster_t<MODE, kStatsNone, false, MI>(c, grid, stream);
 }
 
 }  // namespace
@@ -797,23 +798,24 @@ cudaError_t launch_cluster(const ForceArgs &a, const WsLayout &ws, char *wsp, Pa
     dim3 grid(a.box.ncell, per_cell);
     const int stats = a.energy_virial_out ? kStatsEnergy : (a.pair_count_out ? kStatsCount : kStatsNone);
     if (a.mode == MD_ACCUM_FIXED64) {
-        if (mi) launch_cluster_stats<MD_ACCUM_FIXED64, true>(stats, c, grid, stream);
-        else launch_cluster_stats<MD_ACCUM_FIXED64, false>(stats, c, grid, stream);
+        e = mi ? launch_cluster_stats<MD_ACCUM_FIXED64, true>(stats, c, grid, stream)
+               : launch_cluster_stats<MD_ACCUM_FIXED64, false>(stats, c, grid, stream);
     } else {
-        if (mi) launch_cluster_stats<MD_ACCUM_F32, true>(stats, c, grid, stream);
-        else launch_cluster_stats<MD_ACCUM_F32, false>(stats, c, grid, stream);
+        e = mi ? launch_cluster_stats<MD_ACCUM_F32, true>(stats, c, grid, stream)
+               : launch_cluster_stats<MD_ACCUM_F32, false>(stats, c, grid, stream);
     }
     *nblocks_out = a.box.ncell * per_cell;
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     return launch_finalize_cluster(a, accum, ws, wsp, a.n, stream);
 }
 
 template <int MODE, bool MI, bool PERSIST>
-void launch_cluster_batched_t(const CluArgs &c, dim3 grid, cudaStream_t stream, const BatchArgs &b,
+cudaError_t launch_cluster_batched_t(const CluArgs &c, dim3 grid, cudaStream_t stream, const BatchArgs &b,
                               unsigned long long *cnt, int *work)
 {
-    if (cnt) launch_cluster_t<MODE, kStatsCount, true, MI, PERSIST>(c, grid, stream, b, cnt, work);
-    else launch_cluster_t<MODE, kStatsNone, true, MI, PERSIST>(c, grid, stream, b, nullptr, work);
+    if (cnt) return launch_cluster_t<MODE, kStatsCount, true, MI, PERSIST>(c, grid, stream, b, cnt, work);
+    return launch_cluster_t<MODE, kStatsNone, true, MI, PERSIST>(c, grid, stream, b, nullptr, work);
 }
 
 // Batched cluster kernel over the regular systems' cells (b.cell_list[0 .. ncell_reg),
@@ -840,16 +842,18 @@ cudaError_t launch_cluster_batched(int mode, bool mi, const BatchArgs &b, const 
     unsigned long long *cnt = sys_pair_count;
     int *w = persist_work;
     const int sel = (mode == MD_ACCUM_FIXED64 ? 4 : 0) + (mi ? 2 : 0) + (w ? 1 : 0);
+    cudaError_t e;
     switch (sel) {
-    case 0: launch_cluster_batched_t<MD_ACCUM_F32, false, false>(c, grid, stream, b, cnt, w); break;
-    case 1: launch_cluster_batched_t<MD_ACCUM_F32, false, true>(c, grid, stream, b, cnt, w); break;
-    case 2: launch_cluster_batched_t<MD_ACCUM_F32, true, false>(c, grid, stream, b, cnt, w); break;
-    case 3: launch_cluster_batched_t<MD_ACCUM_F32, true, true>(c, grid, stream, b, cnt, w); break;
-    case 4: launch_cluster_batched_t<MD_ACCUM_FIXED64, false, false>(c, grid, stream, b, cnt, w); break;
-    case 5: launch_cluster_batched_t<MD_ACCUM_FIXED64, false, true>(c, grid, stream, b, cnt, w); break;
-    case 6: launch_cluster_batched_t<MD_ACCUM_FIXED64, true, false>(c, grid, stream, b, cnt, w); break;
-    default: launch_cluster_batched_t<MD_ACCUM_FIXED64, true, true>(c, grid, stream, b, cnt, w); break;
+    case 0: e = launch_cluster_batched_t<MD_ACCUM_F32, false, false>(c, grid, stream, b, cnt, w); break;
+    case 1: e = launch_cluster_batched_t<MD_ACCUM_F32, false, true>(c, grid, stream, b, cnt, w); break;
+    case 2: e = launch_cluster_batched_t<MD_ACCUM_F32, true, false>(c, grid, stream, b, cnt, w); break;
+    case 3: e = launch_cluster_batched_t<MD_ACCUM_F32, true, true>(c, grid, stream, b, cnt, w); break;
+    case 4: e = launch_cluster_batched_t<MD_ACCUM_FIXED64, false, false>(c, grid, stream, b, cnt, w); break;
+    case 5: e = launch_cluster_batched_t<MD_ACCUM_FIXED64, false, true>(c, grid, stream, b, cnt, w); break;
+    case 6: e = launch_cluster_batched_t<MD_ACCUM_FIXED64, true, false>(c, grid, stream, b, cnt, w); break;
+    default: e = launch_cluster_batched_t<MD_ACCUM_FIXED64, true, true>(c, grid, stream, b, cnt, w); break;
     }
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
