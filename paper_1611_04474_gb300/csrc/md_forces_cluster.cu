@@ -212,16 +212,16 @@ __device__ __forceinline__ void cluster_boxes(const float4 *p, int m, float (*bo
 
 // Shared tiles of one CTA.  Reactions: F32 one array per warp (plain read-modify-write,
 // no float atomics); FIXED64 one array for the CTA (native integer shared atomics).
+// Home forces need no array: each home cluster's sums go to global memory per row.
 template <int MODE>
 struct CluSmem {
     using Acc = typename AccT<MODE>::T;
     static constexpr int NW = MODE == MD_ACCUM_FIXED64 ? 1 : kCW;
     float4 hp[kCTile];  // home tile (x, y, z shifted, q)
     float4 np[kCTile];  // neighbour tile
-    int ht[kCTile], nt[kCTile];
+    unsigned char ht[kCTile], nt[kCTile];  // LJ types (below kMaxTypes = 32)
     float ib[6][kCTile / kCS];  // home cluster boxes: lo xyz, hi xyz (one row per bound)
     float jb[6][kCTile / kCS];  // neighbour cluster boxes
-    Acc hf[3][kCTile];          // forces on home atoms (whole cell pair)
     // reactions on neighbour atoms (this tile), component d of atom t at d * kRow + t;
     // F32 rows are 8 words longer, so that the three lanes that add the x, y and z of
     // one atom hit different banks
@@ -232,6 +232,8 @@ struct CluSmem {
 };
 
 struct CluConst {
+    void *accum;  // cluster-order accumulators (global); home sums go there per row
+    int n, hbase; // atoms; slot of the home tile's first atom
     float kc, rc2, rc2m;
     float lo[3];
     float L[3], Lhi[3], Llo[3], invL[3];  // per-pair minimum image (boxes with a 2-cell axis)
@@ -420,7 +422,9 @@ __device__ __forceinline__ void cluster_row(CluSmem<MODE> &sm, const float2 *s_a
     // home-atom sums over the 8 lanes that share them (the home cluster belongs to this
     // warp alone within the CTA): a reduce-scatter of the six (atom, component) sums over
     // the lane bits of jl, after which lane jl < 6 holds sum jl (atom ia0 for jl < 3,
-    // ia1 above, component jl % 3) and adds it to the home tile
+    // ia1 above, component jl % 3) and adds it to the global accumulator (a home
+    // cluster meets each neighbour tile once, so there is nothing to gather in shared
+    // memory first)
     if (MODE != MD_ACCUM_FIXED64) {
         float a, b;
         f2_split(ax2, a, b);
@@ -446,7 +450,15 @@ __device__ __forceinline__ void cluster_row(CluSmem<MODE> &sm, const float2 *s_a
     }
     if (jl < 6) {
         const int ia = jl < 3 ? ia0 : ia1;
-        if (ia < mh) sm.hf[jl < 3 ? jl : jl - 3][ia] += w[0];
+        if (ia < mh) {
+            const size_t s = (size_t)(k.hbase + ia);
+            const int d = jl < 3 ? jl : jl - 3;
+            if (MODE == MD_ACCUM_FIXED64)
+                atomicAdd(static_cast<unsigned long long *>(k.accum) + (size_t)d * k.n + s,
+                          (unsigned long long)w[0]);
+            else
+                atomicAdd(static_cast<float *>(k.accum) + 4 * s + d, (float)w[0]);
+        }
     }
 }
 
@@ -520,6 +532,8 @@ __device__ __forceinline__ void cluster_item(CluSmem<MODE> &sm, float2 *s_ab, co
         return;
     }
     k.status = a.status;
+    k.accum = a.accum;
+    k.n = a.n;
     bool shift = false;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -533,6 +547,7 @@ __device__ __forceinline__ void cluster_item(CluSmem<MODE> &sm, float2 *s_ab, co
 
     for (int h0 = 0; h0 < nh; h0 += kCTile) {
         const int mh = min(kCTile, nh - h0);
+        k.hbase = h_begin + h0;
         const int nic = (mh + kCS - 1) / kCS;
         __syncthreads();
         for (int t = threadIdx.x; t < nic * kCS; t += kCT) {
@@ -548,8 +563,7 @@ __device__ __forceinline__ void cluster_item(CluSmem<MODE> &sm, float2 *s_ab, co
                 p = make_float4(kFar, kFar, kFar, 0.f);
             }
             sm.hp[t] = p;
-            sm.ht[t] = ty;
-            sm.hf[0][t] = sm.hf[1][t] = sm.hf[2][t] = Acc(0);
+            sm.ht[t] = (unsigned char)ty;
         }
         __syncthreads();
         cluster_boxes(sm.hp, mh, sm.ib);
@@ -574,7 +588,7 @@ __device__ __forceinline__ void cluster_item(CluSmem<MODE> &sm, float2 *s_ab, co
                     ty = clamp_type(a.ty[n_begin + n0 + t], k.T, a.status);
                 }
                 sm.np[t] = p;
-                sm.nt[t] = ty;
+                sm.nt[t] = (unsigned char)ty;
 #pragma unroll
                 for (int w = 0; w < CluSmem<MODE>::NW; ++w) sm.react(w, 0, t) = sm.react(w, 1, t) = sm.react(w, 2, t) = Acc(0);
             }
@@ -603,12 +617,7 @@ __device__ __forceinline__ void cluster_item(CluSmem<MODE> &sm, float2 *s_ab, co
                     sy += sm.react(w, 1, t);
                     sz += sm.react(w, 2, t);
                 }
-                if (diag) {
-                    // the neighbour tile is the home tile: reactions join the home sums
-                    sm.hf[0][t] += sx;
-                    sm.hf[1][t] += sy;
-                    sm.hf[2][t] += sz;
-                } else {
+                {
                     const int s = n_begin + n0 + t;
                     if (MODE == MD_ACCUM_FIXED64) {
                         unsigned long long *acc = static_cast<unsigned long long *>(a.accum);
@@ -619,19 +628,6 @@ __device__ __forceinline__ void cluster_item(CluSmem<MODE> &sm, float2 *s_ab, co
                         red_add_v4(static_cast<float4 *>(a.accum) + s, (float)sx, (float)sy, (float)sz);
                     }
                 }
-            }
-        }
-        __syncthreads();
-        for (int t = threadIdx.x; t < mh; t += kCT) {
-            const int s = h_begin + h0 + t;
-            if (MODE == MD_ACCUM_FIXED64) {
-                unsigned long long *acc = static_cast<unsigned long long *>(a.accum);
-                atomicAdd(&acc[s], (unsigned long long)sm.hf[0][t]);
-                atomicAdd(&acc[(size_t)a.n + s], (unsigned long long)sm.hf[1][t]);
-                atomicAdd(&acc[2 * (size_t)a.n + s], (unsigned long long)sm.hf[2][t]);
-            } else {
-                red_add_v4(static_cast<float4 *>(a.accum) + s, (float)sm.hf[0][t], (float)sm.hf[1][t],
-                           (float)sm.hf[2][t]);
             }
         }
     }
@@ -646,13 +642,16 @@ __device__ __forceinline__ void cluster_item(CluSmem<MODE> &sm, float2 *s_ab, co
 // wave whose CTAs take cell pairs from a counter until none are left (`work`, zeroed
 // before the launch; items ordered stencil entry-major like the plain grid).
 // Register budget: 8 CTAs per SM (64 registers a thread), which the force, step and
-// pair-counting forms fit without spilling.  Summing energies carries more live values
-// (7 CTAs for FP32, 6 for FIXED64), and so does the persistent FIXED64 counting form (6).
+// pair-counting forms fit without spilling; the FP32 force and step form takes 9 (56
+// registers, and its shared memory fits 9 as well).  Summing energies carries more live
+// values (7 CTAs for FP32, 6 for FIXED64), and so does the persistent FIXED64 counting
+// form (6).
 template <int MODE, int STATS, bool PERSIST>
 constexpr int clu_min_blocks()
 {
     return STATS == kStatsEnergy ? (MODE == MD_ACCUM_FIXED64 ? 6 : 7)
-         : (MODE == MD_ACCUM_FIXED64 && STATS != kStatsNone && PERSIST) ? 6 : 8;
+         : (MODE == MD_ACCUM_FIXED64 && STATS != kStatsNone && PERSIST) ? 6
+         : (MODE == MD_ACCUM_F32 && STATS == kStatsNone) ? 9 : 8;
 }
 
 template <int MODE, int STATS, bool BATCHED, bool MI, bool PERSIST>
