@@ -187,7 +187,7 @@ __device__ __forceinline__ void block_scan_cells(int *__restrict__ cnt_cursor, i
 
 // One velocity-Verlet half step per atom and its cell: v += dt/2 a (when kick), x <-
 // wrap(x + dt v), the float copy (x, y, z, q), the cell index and the histogram; the
-// work of k_kick, k_drift_wrap and k_cell_index in one pass.  BATCHED: each atom's box
+// work of a kick, a drift with wrap and k_cell_index in one pass.  BATCHED: each atom's box
 // from its system, cells numbered over the batch.  It also zeroes the force kernels'
 // cluster-order accumulators (`accum`, MD_ACCUM_F32 float4[n] or MD_ACCUM_FIXED64
 // u64[3][n]; null for none) and the persistent launches' item counters (`work`, may be
