@@ -174,3 +174,34 @@ def test_step_cells_of_every_size(cuda_lib, side):
     F = api.forces_to_f64(eng.forces, api.ACCUM_FIXED64).cpu().numpy()
     err = force_errors(F, r.F, r.cond, alts)
     assert err["max_norm"] <= 1e-5, err
+
+
+def test_step_on_a_grid_of_more_than_1024_cells(cuda_lib):
+    """The MD step's cell build on a grid too large for the per-block shared histogram
+    (16 x 16 x 11 = 2,816 cells): counts by global atomics, a separate scan, per-cell
+    bins. In FIXED64 the forces md_step computes equal md_nonbonded_forces' bit for bit
+    at the same positions, before and after two steps, so both cell lists hold the same
+    pairs."""
+    api = cuda_lib
+    s = W.lattice_box(n=20000, seed=21, ntypes=4, rc=4.0).with_forcefield(0.5, (12.0, 16.0), seed=5)
+    assert np.prod(np.floor(np.asarray(s.box) / s.rc)) > 1024
+
+    def reference(sys_):
+        ref = api.Engine(sys_, mode=api.ACCUM_FIXED64)
+        ref.build_cells()
+        ref.compute_forces()
+        torch.cuda.synchronize()
+        assert int(ref.status.item()) == 0
+        return ref.forces.cpu().numpy()
+
+    eng = api.Engine(s, mode=api.ACCUM_FIXED64)
+    eng.step(0, dt_fs=0.5)
+    torch.cuda.synchronize()
+    assert int(eng.status.item()) == 0
+    assert np.array_equal(eng.forces.cpu().numpy(), reference(s))
+    eng.step(2, dt_fs=0.5)
+    torch.cuda.synchronize()
+    assert int(eng.status.item()) == 0
+    p = eng.pos.cpu().numpy().astype(np.float32)
+    s1 = W.System(s.name, p, s.q, s.type, s.box, s.rc, s.sigma, s.eps, s.AB, s.mass, s.vel)
+    assert np.array_equal(eng.forces.cpu().numpy(), reference(s1))
