@@ -20,6 +20,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -46,6 +47,21 @@ TRAFFIC_CAPTURE = {"bytes": 3362304, "atoms": 92224,
                    "kernel_source_sha256": "f7e3af0e7f095a588105ad934e768c07d032a775a7246fe0573cc02e34b3160f"}
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1611_04474_gb300", "csrc", f)
                   for f in ("md_forces_cluster.cu", "md_pairgeom.cuh", "md_internal.cuh")]
+
+
+def artifact_dir() -> str:
+    """Where the raw clock and power samples go: $MDNB_ARTIFACT_DIR when set, else a
+    fresh temporary directory (the JSON line carries their summaries either way)."""
+    d = os.environ.get("MDNB_ARTIFACT_DIR")
+    if not d:
+        global _TMP_ARTIFACTS
+        if _TMP_ARTIFACTS is None:
+            _TMP_ARTIFACTS = tempfile.mkdtemp(prefix="mdnb_bench_")
+        d = _TMP_ARTIFACTS
+    return d
+
+
+_TMP_ARTIFACTS = None
 
 
 def kernel_source_sha256() -> str | None:
@@ -128,7 +144,7 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.idx = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+        self.path = os.path.join(artifact_dir(), f"clocks_gpu{gpu_index}.csv")
 
     def start(self):
         try:
@@ -186,7 +202,7 @@ def measure_energy(eng, stream, dev_index: int, seconds: float = 2.0, dt_fs: flo
     b.record(stream)
     torch.cuda.synchronize()
     n_steps = max(100, int(seconds * 1e3 / (a.elapsed_time(b) / 20)))
-    path = os.path.join(ROOT, "gpurun_out", f"power_gpu{dev_index}.csv")
+    path = os.path.join(artifact_dir(), f"power_gpu{dev_index}.csv")
     try:
         os.makedirs(os.path.dirname(path), exist_ok=True)
         f = open(path, "w")

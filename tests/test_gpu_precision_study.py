@@ -12,7 +12,7 @@ drift is reported, not asserted: the paper gives no value for it.
 
 The gentle force field (sigma x 0.5, masses 12-16 amu) keeps the dynamics physical; the
 atoms, charges, box and cutoff are those of the throughput workload.  The report is
-written to gpurun_out/precision_study.json when that folder exists.
+printed, and written to $MDNB_ARTIFACT_DIR/precision_study.json when that is set.
 """
 import hashlib
 import json
@@ -93,8 +93,8 @@ def test_precision_study_92k(cuda_lib):
                     "drift_kcal_per_mol_atom_per_ns": float(slope * 1e6 / s.n),
                     "KE_mean": float(e[:, 2].mean())}
     report["fixed64_sha256"] = hashes
-    out = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
-    if os.path.isdir(out):
+    out = os.environ.get("MDNB_ARTIFACT_DIR")
+    if out and os.path.isdir(out):
         with open(os.path.join(out, "precision_study.json"), "w") as f:
             json.dump(report, f, indent=1)
     print(json.dumps(report, indent=1))
