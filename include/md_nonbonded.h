@@ -168,8 +168,8 @@ int md_build_cells_noalloc(const float *pos_q, const int32_t *type, int32_t n,
  *                 (F = f r); summed per block and then in a fixed order
  *   pair_count_out     device uint64[1] or NULL: unique pairs with r^2 < rc^2
  * Forces and counts of modes FIXED64 and F64 are reproducible bit for bit; F32 adds
- * per-tile sums with floating-point atomics and may differ in the last bits between
- * runs.
+ * partial sums (per home cluster and per tile) with floating-point atomics and may
+ * differ in the last bits between runs.
  */
 int md_nonbonded_forces(const int32_t *cell_start, const int32_t *perm, const float *pos_q_sorted,
                         const int32_t *type_sorted, int32_t n, const double *box_L,
