@@ -55,7 +55,7 @@ extern "C" {
 
 /* device status bits */
 #define MD_STATUS_NONFINITE 1u      /* a non-finite position or force was seen */
-#define MD_STATUS_FIXED_OVERFLOW 2u /* a pair term reached 2^31 kcal/mol/A in MD_ACCUM_FIXED64 */
+#define MD_STATUS_FIXED_OVERFLOW 2u /* a term reached 2^31 kcal/mol/A in a fixed-point mode */
 #define MD_STATUS_BAD_TYPE 4u       /* an LJ type outside [0, ntypes) was read as type 0 */
 
 /* accumulation / precision modes (argument `mode`) */
@@ -66,11 +66,20 @@ extern "C" {
                               forces int64[n][3] (divide by 2^32 for kcal/mol/A) */
 #define MD_ACCUM_F64 2     /* FP64 pair math and accumulation, a slow reference mode;
                               forces double[n][3] */
+#define MD_ACCUM_FIXED_TILE 3 /* FP32 pair math and FP32 partial sums, each partial rounded
+                              once to the int64 grid of MD_ACCUM_FIXED64 and summed exactly:
+                              a home cluster's sums per neighbour tile, and a neighbour
+                              tile's reactions.  The partials are formed in a fixed order
+                              (no floating-point atomics), so results are bit-reproducible
+                              run to run for the same inputs, but they depend on the cell
+                              and cluster order and differ from MD_ACCUM_FIXED64's bits;
+                              forces int64[n][3] as in MD_ACCUM_FIXED64.  Cluster kernel only
+                              (MD_ALGO_DEFAULT or MD_ALGO_CLUSTER; batch shapes 0 and 5) */
 
 /* force-kernel choice for md_nonbonded_forces_algo.  MD_ALGO_DEFAULT (what
  * md_nonbonded_forces and md_step use): MD_ALGO_CLUSTER for MD_ACCUM_F32 and
  * MD_ACCUM_FIXED64, MD_ALGO_FULL_SHELL for MD_ACCUM_F64 (its only kernel). */
-#define MD_ALGO_DEFAULT 0
+#define MD_ALGO_DEFAULT 0 /* MD_ACCUM_FIXED_TILE: MD_ALGO_CLUSTER */
 #define MD_ALGO_FULL_SHELL 1 /* one thread per home atom over all 27 neighbour cells (Alg. 1) */
 #define MD_ALGO_HALF_SHELL 2 /* each cell pair once, reactions by Newton's third law */
 #define MD_ALGO_CLUSTER 3    /* the half shell filtered by clusters of 8 atoms, every pair of
@@ -160,16 +169,17 @@ int md_build_cells_noalloc(const float *pos_q, const int32_t *type, int32_t n,
  * the filter r^2 < rc^2, and only the surviving pairs reach the force computation.
  *   cell_start, perm, pos_q_sorted, type_sorted   as returned by md_build_cells
  *   ff            host pointer to the force field (AB on the device)
- *   mode          MD_ACCUM_F32 / MD_ACCUM_FIXED64 / MD_ACCUM_F64
+ *   mode          MD_ACCUM_F32 / MD_ACCUM_FIXED64 / MD_ACCUM_F64 / MD_ACCUM_FIXED_TILE
  *   forces_out    [n][3] in INPUT atom order; element type by mode (float, int64,
- *                 double); fully overwritten (the callee zeroes it)
+ *                 double, int64); fully overwritten (the callee zeroes it)
  *   energy_virial_out  device double[3] = {E_LJ, E_Coulomb, W} or NULL, with
  *                 U_LJ = A/(12 r^12) - B/(6 r^6), U_C = k q1 q2 / r, W = sum f r^2
  *                 (F = f r); summed per block and then in a fixed order
  *   pair_count_out     device uint64[1] or NULL: unique pairs with r^2 < rc^2
- * Forces and counts of modes FIXED64 and F64 are reproducible bit for bit; F32 adds
- * partial sums (per home cluster and per tile) with floating-point atomics and may
- * differ in the last bits between runs.
+ * Forces and counts of modes FIXED64, F64 and FIXED_TILE are reproducible bit for bit;
+ * F32 adds partial sums (per home cluster and per tile) with floating-point atomics and
+ * may differ in the last bits between runs.  MD_ERR_INVALID_ARG for MD_ACCUM_FIXED_TILE
+ * with MD_ALGO_FULL_SHELL or MD_ALGO_HALF_SHELL.
  */
 int md_nonbonded_forces(const int32_t *cell_start, const int32_t *perm, const float *pos_q_sorted,
                         const int32_t *type_sorted, int32_t n, const double *box_L,
@@ -235,7 +245,8 @@ int md_batch_prepare(int32_t nsys, const md_system_desc *systems, void *workspac
                      size_t ws_bytes, void *stream);
 
 /* md_step for a batch prepared in `workspace` with the same `systems` (host).  Arrays
- * are the concatenations described above; mode MD_ACCUM_F32 or MD_ACCUM_FIXED64.
+ * are the concatenations described above; mode MD_ACCUM_F32, MD_ACCUM_FIXED64 or
+ * MD_ACCUM_FIXED_TILE (the last with shapes 0 and 5 only, else MD_ERR_INVALID_ARG).
  * pair_count: device uint64[nsys] or NULL; the unique within-cutoff pairs of every
  * force evaluation are added to it (the caller zeroes it).  Makes no host<->device
  * copies and no allocation, so a sequence of calls can be captured in a CUDA graph

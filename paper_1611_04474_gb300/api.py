@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libmdnb.so")
 ACCUM_F32 = 0
 ACCUM_FIXED64 = 1
 ACCUM_F64 = 2
+ACCUM_FIXED_TILE = 3
 ALGO_DEFAULT = 0
 ALGO_FULL_SHELL = 1
 ALGO_HALF_SHELL = 2
@@ -135,7 +136,8 @@ def _dims(dims):
     return (ctypes.c_int32 * 3)(*[int(x) for x in dims])
 
 
-FORCE_DTYPE = {ACCUM_F32: torch.float32, ACCUM_FIXED64: torch.int64, ACCUM_F64: torch.float64}
+FORCE_DTYPE = {ACCUM_F32: torch.float32, ACCUM_FIXED64: torch.int64, ACCUM_F64: torch.float64,
+               ACCUM_FIXED_TILE: torch.int64}
 
 
 class ForceField:
@@ -257,7 +259,7 @@ def step(pos, vel, forces, forces_valid: bool, inv_mass, q, types, box, ff: Forc
 
 def forces_to_f64(F: torch.Tensor, mode: int) -> torch.Tensor:
     """Forces of any mode as float64 kcal/mol/A."""
-    if mode == ACCUM_FIXED64:
+    if mode in (ACCUM_FIXED64, ACCUM_FIXED_TILE):
         return F.to(torch.float64) / FIXED_SCALE
     return F.to(torch.float64)
 
@@ -319,8 +321,8 @@ class Batch:
 
     def __init__(self, systems, mode=ACCUM_FIXED64, device="cuda", state=None, ffs=None,
                  tuning=(0, 0)):
-        if mode not in (ACCUM_F32, ACCUM_FIXED64):
-            raise ValueError("batched mode must be ACCUM_F32 or ACCUM_FIXED64")
+        if mode not in (ACCUM_F32, ACCUM_FIXED64, ACCUM_FIXED_TILE):
+            raise ValueError("batched mode must be ACCUM_F32, ACCUM_FIXED64 or ACCUM_FIXED_TILE")
         self.systems = list(systems)
         self.mode = mode
         self.nsys = len(self.systems)

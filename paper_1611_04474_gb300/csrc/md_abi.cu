@@ -243,9 +243,13 @@ int md_nonbonded_forces_algo(const int32_t *cell_start, const int32_t *perm,
     if (n < 0 || n > kMaxAtoms) return MD_ERR_INVALID_ARG;
     int e = check_ff(ff);
     if (e) return e;
-    if (mode != MD_ACCUM_F32 && mode != MD_ACCUM_FIXED64 && mode != MD_ACCUM_F64) return MD_ERR_INVALID_ARG;
+    if (mode != MD_ACCUM_F32 && mode != MD_ACCUM_FIXED64 && mode != MD_ACCUM_F64 &&
+        mode != MD_ACCUM_FIXED_TILE)
+        return MD_ERR_INVALID_ARG;
     if (algo != MD_ALGO_DEFAULT && algo != MD_ALGO_FULL_SHELL && algo != MD_ALGO_HALF_SHELL &&
         algo != MD_ALGO_CLUSTER)
+        return MD_ERR_INVALID_ARG;
+    if (mode == MD_ACCUM_FIXED_TILE && algo != MD_ALGO_DEFAULT && algo != MD_ALGO_CLUSTER)
         return MD_ERR_INVALID_ARG;
     int32_t want[3];
     if ((e = compute_dims(box_L, ff->rc, want))) return e;
@@ -301,7 +305,9 @@ int md_step(double *pos, double *vel, void *forces, int32_t forces_valid, const 
     if (!(dt_fs > 0.0) || !isfinite(dt_fs)) return MD_ERR_INVALID_ARG;
     int e = check_ff(ff);
     if (e) return e;
-    if (mode != MD_ACCUM_F32 && mode != MD_ACCUM_FIXED64 && mode != MD_ACCUM_F64) return MD_ERR_INVALID_ARG;
+    if (mode != MD_ACCUM_F32 && mode != MD_ACCUM_FIXED64 && mode != MD_ACCUM_F64 &&
+        mode != MD_ACCUM_FIXED_TILE)
+        return MD_ERR_INVALID_ARG;
     int32_t dims[3];
     if ((e = compute_dims(box_L, ff->rc, dims))) return e;
     if (n > 0 && (!pos || !vel || !forces || !inv_mass || !q || !type)) return MD_ERR_INVALID_ARG;
@@ -459,7 +465,12 @@ int md_batch_step_tuned(int32_t nsys, const md_system_desc *systems, double *pos
     int e = batch_layout(nsys, systems, &bl, &dims);
     if (e) return e;
     if (n_steps < 0 || !(dt_fs > 0.0) || !isfinite(dt_fs)) return MD_ERR_INVALID_ARG;
-    if (mode != MD_ACCUM_F32 && mode != MD_ACCUM_FIXED64) return MD_ERR_INVALID_ARG;
+    if (mode != MD_ACCUM_F32 && mode != MD_ACCUM_FIXED64 && mode != MD_ACCUM_FIXED_TILE)
+        return MD_ERR_INVALID_ARG;
+    // MD_ACCUM_FIXED_TILE runs on the cluster kernel only: shapes 0 and 5
+    if (mode == MD_ACCUM_FIXED_TILE &&
+        ((shape_reg != 0 && shape_reg != 5) || (shape_mi != 0 && shape_mi != 5)))
+        return MD_ERR_INVALID_ARG;
     if (bl.n > 0 && (!pos || !vel || !forces || !inv_mass || !q || !type)) return MD_ERR_INVALID_ARG;
     if (!workspace) return MD_ERR_WORKSPACE;
     uintptr_t p = reinterpret_cast<uintptr_t>(workspace);

@@ -210,6 +210,8 @@ cudaError_t launch_forces(const ForceArgs &a, const WsLayout &ws, char *wsp, cud
     int algo = a.algo;
     if (algo == MD_ALGO_DEFAULT || a.mode == MD_ACCUM_F64)
         algo = a.mode == MD_ACCUM_F64 ? MD_ALGO_FULL_SHELL : MD_ALGO_CLUSTER;
+    // MD_ACCUM_FIXED_TILE exists in the cluster kernel only (the ABI rejects other kernels)
+    if (a.mode == MD_ACCUM_FIXED_TILE && algo != MD_ALGO_CLUSTER) return cudaErrorInvalidValue;
     int nblocks = a.box.ncell;
     if (algo == MD_ALGO_CLUSTER) {
         cudaError_t e = launch_cluster(a, ws, wsp, partials, &nblocks, stream);

@@ -76,7 +76,7 @@ k_cluster_order(const int32_t *__restrict__ cell_start, const float4 *__restrict
     if (m <= 0) return;
     // the force kernel's accumulators of this cell's slots start at zero
     for (int t = threadIdx.x; t < m; t += kOrderThreads) {
-        if (mode == MD_ACCUM_FIXED64) {
+        if (fixed_output(mode)) {
             unsigned long long *A = static_cast<unsigned long long *>(accum);
             A[b + t] = 0ull;
             A[(size_t)n + b + t] = 0ull;
@@ -456,6 +456,9 @@ __device__ __forceinline__ void cluster_row(CluSmem<MODE> &sm, const float2 *s_a
             if (MODE == MD_ACCUM_FIXED64)
                 atomicAdd(static_cast<unsigned long long *>(k.accum) + (size_t)d * k.n + s,
                           (unsigned long long)w[0]);
+            else if (MODE == MD_ACCUM_FIXED_TILE)  // this row's sum, rounded once
+                atomicAdd(static_cast<unsigned long long *>(k.accum) + (size_t)d * k.n + s,
+                          (unsigned long long)to_fixed((float)w[0], k.status));
             else
                 atomicAdd(static_cast<float *>(k.accum) + 4 * s + d, (float)w[0]);
         }
@@ -596,7 +599,9 @@ __device__ __forceinline__ void cluster_item(CluSmem<MODE> &sm, float2 *s_ab, co
             cluster_boxes(sm.np, mn, sm.jb);
             if (threadIdx.x == 0) sm.next = kCW;
             __syncthreads();
-            // home clusters handed out one at a time, so that warps finish together
+            // home clusters handed out one at a time, so that warps finish together;
+            // MD_ACCUM_FIXED_TILE deals them in a fixed order (warp w takes w, w + kCW, ...)
+            // so that every warp-private partial sum is formed in the same order each run
             for (int ic = warp; ic < nic;) {
                 if (diag)
                     cluster_row<MODE, STATS, true, false, MI>(sm, s_ab, k, ic, njc, mh, warp, lane, e_lj, e_c, vir, cnt);
@@ -604,9 +609,13 @@ __device__ __forceinline__ void cluster_item(CluSmem<MODE> &sm, float2 *s_ab, co
                     cluster_row<MODE, STATS, false, true, false>(sm, s_ab, k, ic, njc, mh, warp, lane, e_lj, e_c, vir, cnt);
                 else
                     cluster_row<MODE, STATS, false, false, MI>(sm, s_ab, k, ic, njc, mh, warp, lane, e_lj, e_c, vir, cnt);
-                int nx = 0;
-                if (lane == 0) nx = atomicAdd(&sm.next, 1);
-                ic = __shfl_sync(0xffffffffu, nx, 0);
+                if (MODE == MD_ACCUM_FIXED_TILE) {
+                    ic += kCW;
+                } else {
+                    int nx = 0;
+                    if (lane == 0) nx = atomicAdd(&sm.next, 1);
+                    ic = __shfl_sync(0xffffffffu, nx, 0);
+                }
             }
             __syncthreads();
             for (int t = threadIdx.x; t < mn; t += kCT) {
@@ -624,6 +633,13 @@ __device__ __forceinline__ void cluster_item(CluSmem<MODE> &sm, float2 *s_ab, co
                         atomicAdd(&acc[s], (unsigned long long)sx);
                         atomicAdd(&acc[(size_t)a.n + s], (unsigned long long)sy);
                         atomicAdd(&acc[2 * (size_t)a.n + s], (unsigned long long)sz);
+                    } else if (MODE == MD_ACCUM_FIXED_TILE) {
+                        // the tile's reaction on this atom (warps summed in a fixed
+                        // order), rounded once
+                        unsigned long long *acc = static_cast<unsigned long long *>(a.accum);
+                        atomicAdd(&acc[s], (unsigned long long)to_fixed((float)sx, a.status));
+                        atomicAdd(&acc[(size_t)a.n + s], (unsigned long long)to_fixed((float)sy, a.status));
+                        atomicAdd(&acc[2 * (size_t)a.n + s], (unsigned long long)to_fixed((float)sz, a.status));
                     } else {
                         red_add_v4(static_cast<float4 *>(a.accum) + s, (float)sx, (float)sy, (float)sz);
                     }
@@ -651,7 +667,7 @@ constexpr int clu_min_blocks()
 {
     return STATS == kStatsEnergy ? (MODE == MD_ACCUM_FIXED64 ? 6 : 7)
          : (MODE == MD_ACCUM_FIXED64 && STATS != kStatsNone && PERSIST) ? 6
-         : (MODE == MD_ACCUM_F32 && STATS == kStatsNone) ? 9 : 8;
+         : (MODE != MD_ACCUM_FIXED64 && STATS == kStatsNone) ? 9 : 8;
 }
 
 template <int MODE, int STATS, bool BATCHED, bool MI, bool PERSIST>
@@ -766,7 +782,7 @@ cudaError_t launch_cluster_stats(int stats, const CluArgs &c, dim3 grid, cudaStr
 cudaError_t launch_cluster(const ForceArgs &a, const WsLayout &ws, char *wsp, Partial *partials,
                            int *nblocks_out, cudaStream_t stream)
 {
-    const size_t acc_bytes = (size_t)a.n * (a.mode == MD_ACCUM_FIXED64 ? 24 : 16);
+    const size_t acc_bytes = (size_t)a.n * (fixed_output(a.mode) ? 24 : 16);
     void *accum = wsp + ws.accum;
     float4 *cpq = reinterpret_cast<float4 *>(wsp + ws.clu_pos_q);
     int32_t *cty = reinterpret_cast<int32_t *>(wsp + ws.clu_type);
@@ -799,6 +815,9 @@ cudaError_t launch_cluster(const ForceArgs &a, const WsLayout &ws, char *wsp, Pa
     if (a.mode == MD_ACCUM_FIXED64) {
         e = mi ? launch_cluster_stats<MD_ACCUM_FIXED64, true>(stats, c, grid, stream)
                : launch_cluster_stats<MD_ACCUM_FIXED64, false>(stats, c, grid, stream);
+    } else if (a.mode == MD_ACCUM_FIXED_TILE) {
+        e = mi ? launch_cluster_stats<MD_ACCUM_FIXED_TILE, true>(stats, c, grid, stream)
+               : launch_cluster_stats<MD_ACCUM_FIXED_TILE, false>(stats, c, grid, stream);
     } else {
         e = mi ? launch_cluster_stats<MD_ACCUM_F32, true>(stats, c, grid, stream)
                : launch_cluster_stats<MD_ACCUM_F32, false>(stats, c, grid, stream);
@@ -840,7 +859,7 @@ cudaError_t launch_cluster_batched(int mode, bool mi, const BatchArgs &b, const 
     dim3 grid(ncells, mi ? 27 : 14);
     unsigned long long *cnt = sys_pair_count;
     int *w = persist_work;
-    const int sel = (mode == MD_ACCUM_FIXED64 ? 4 : 0) + (mi ? 2 : 0) + (w ? 1 : 0);
+    const int sel = (mode == MD_ACCUM_FIXED64 ? 4 : mode == MD_ACCUM_FIXED_TILE ? 8 : 0) + (mi ? 2 : 0) + (w ? 1 : 0);
     cudaError_t e;
     switch (sel) {
     case 0: e = launch_cluster_batched_t<MD_ACCUM_F32, false, false>(c, grid, stream, b, cnt, w); break;
@@ -850,7 +869,11 @@ cudaError_t launch_cluster_batched(int mode, bool mi, const BatchArgs &b, const 
     case 4: e = launch_cluster_batched_t<MD_ACCUM_FIXED64, false, false>(c, grid, stream, b, cnt, w); break;
     case 5: e = launch_cluster_batched_t<MD_ACCUM_FIXED64, false, true>(c, grid, stream, b, cnt, w); break;
     case 6: e = launch_cluster_batched_t<MD_ACCUM_FIXED64, true, false>(c, grid, stream, b, cnt, w); break;
-    default: e = launch_cluster_batched_t<MD_ACCUM_FIXED64, true, true>(c, grid, stream, b, cnt, w); break;
+    case 7: e = launch_cluster_batched_t<MD_ACCUM_FIXED64, true, true>(c, grid, stream, b, cnt, w); break;
+    case 8: e = launch_cluster_batched_t<MD_ACCUM_FIXED_TILE, false, false>(c, grid, stream, b, cnt, w); break;
+    case 9: e = launch_cluster_batched_t<MD_ACCUM_FIXED_TILE, false, true>(c, grid, stream, b, cnt, w); break;
+    case 10: e = launch_cluster_batched_t<MD_ACCUM_FIXED_TILE, true, false>(c, grid, stream, b, cnt, w); break;
+    default: e = launch_cluster_batched_t<MD_ACCUM_FIXED_TILE, true, true>(c, grid, stream, b, cnt, w); break;
     }
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
@@ -867,7 +890,7 @@ cudaError_t launch_finalize_cluster(const ForceArgs &a, const void *accum, const
     const bool kick = a.kick_vel != nullptr;
     const dim3 blk(256);
     cudaError_t e;
-    if (a.mode == MD_ACCUM_FIXED64) {
+    if (fixed_output(a.mode)) {  // int64 accumulators (FIXED64 and FIXED_TILE alike)
         if (kick)
             e = launch_pdl(k_finalize_clu<MD_ACCUM_FIXED64, true>, dim3(g), blk, 0, stream, accum, corder, a.perm, n, a.forces_out, a.status, a.kick_vel, a.kick_inv_mass, a.kick_half_dt);
         else

@@ -571,7 +571,11 @@ cudaError_t launch_forces_batched(const ForceArgs &a, const BatchArgs &b,
                                   char *wsp, cudaStream_t stream, int shape_reg, int shape_mi)
 {
     Partial *partials = reinterpret_cast<Partial *>(wsp + ws.partials);
-    const size_t acc_bytes = (size_t)b.n * (a.mode == MD_ACCUM_FIXED64 ? 24 : 16);
+    const size_t acc_bytes = (size_t)b.n * (fixed_output(a.mode) ? 24 : 16);
+    // MD_ACCUM_FIXED_TILE runs on the cluster kernel only (shapes 0 and 5)
+    if (a.mode == MD_ACCUM_FIXED_TILE && ((b.ncell_reg > 0 && shape_reg != 0 && shape_reg != 5) ||
+                                          (b.ncell_mi > 0 && shape_mi != 0 && shape_mi != 5)))
+        return cudaErrorInvalidValue;
     void *accum = wsp + ws.accum;
     cudaError_t e = a.accum_zeroed ? cudaSuccess : cudaMemsetAsync(accum, 0, acc_bytes, stream);
     if (e != cudaSuccess) return e;

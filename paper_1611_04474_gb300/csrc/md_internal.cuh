@@ -19,6 +19,12 @@ constexpr float kFixedLimit = 2147483648.0f;
 
 constexpr int kMaxTypes = 32;
 
+// Modes whose forces are int64 at 2^-32 (accumulators u64[3][n], output int64[n][3]).
+__host__ __device__ constexpr bool fixed_output(int mode)
+{
+    return mode == MD_ACCUM_FIXED64 || mode == MD_ACCUM_FIXED_TILE;
+}
+
 // Per-block partial results of a force or kinetic-energy pass, reduced later in a
 // fixed order so that sums do not depend on block scheduling.
 struct Partial {
@@ -250,7 +256,7 @@ __device__ __forceinline__ void load_force(const void *forces, int mode, int i, 
         f[0] = F[3 * i];
         f[1] = F[3 * i + 1];
         f[2] = F[3 * i + 2];
-    } else if (mode == MD_ACCUM_FIXED64) {
+    } else if (fixed_output(mode)) {
         const long long *F = static_cast<const long long *>(forces);
         const double s = 1.0 / 4294967296.0;
         f[0] = (double)F[3 * i] * s;

@@ -121,6 +121,11 @@ template <>
 struct AccT<MD_ACCUM_FIXED64> {
     using T = unsigned long long;
 };
+// MD_ACCUM_FIXED_TILE sums in FP32 within a tile and rounds the partials to int64
+template <>
+struct AccT<MD_ACCUM_FIXED_TILE> {
+    using T = float;
+};
 
 __device__ __forceinline__ void red_add_v4(float4 *addr, float a, float b, float c)
 {

@@ -101,3 +101,27 @@ def test_host_validation_rejects_before_any_launch(lib):
     # md_step: dt <= 0
     assert lib.md_step(None, None, None, 0, None, None, None, 0, box, ctypes.byref(ff), 0, 0.0, 1,
                        None, None, 0, None, None) == -1
+
+
+def test_fixed_tile_mode_only_on_the_cluster_kernel(lib):
+    from paper_1611_04474_gb300 import api
+
+    box = (ctypes.c_double * 3)(10.0, 10.0, 10.0)
+    dims = (ctypes.c_int32 * 3)(3, 3, 3)
+    cs = ctypes.c_void_p(16)  # never dereferenced: validation fails first
+    ff = api.md_forcefield(4, 0, 256, 332.0636, 3.0)
+    for algo in (api.ALGO_FULL_SHELL, api.ALGO_HALF_SHELL):
+        assert lib.md_nonbonded_forces_algo(cs, None, None, None, 0, box, dims, ctypes.byref(ff),
+                                            api.ACCUM_FIXED_TILE, algo, None, None, None, None, 0,
+                                            None, None) == -1
+    # batched: shapes 1..4 are the half-shell kernel
+    desc = (api.md_system_desc * 1)()
+    desc[0].n = 10
+    for d in range(3):
+        desc[0].box_L[d] = 10.0
+    desc[0].ff = ff
+    for shape in (1, 2, 3, 4):
+        t = api.md_batch_tuning(shape, 0)
+        assert lib.md_batch_step_tuned(1, ctypes.byref(desc), None, None, None, 0, None, None,
+                                       None, api.ACCUM_FIXED_TILE, 1.0, 1, None, None, 0, None,
+                                       ctypes.byref(t), None) == -1
