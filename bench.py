@@ -31,8 +31,10 @@ sys.path.insert(0, ROOT)
 METRIC = "within-cutoff pair interactions/sec"
 UNIT = "pairs/s"
 L2_FLUSH_BYTES = 256 << 20  # twice the 129 MB L2
+# nominal FP32 multiply-add peak (context only; the roofline uses the measured figure)
 FP32_LANES_PER_SM = 128
-NUM_SMS = 152
+NOMINAL_SMS = 152
+NOMINAL_SM_GHZ = 2.07
 # algorithmic FLOPs (FMA = 2): per half-shell candidate pair (3 sub, 3 mul, 2 add) and
 # per surviving pair (powers, Eq. 1-2 factor, F = f r, reaction)
 FLOP_PER_CANDIDATE = 8
@@ -40,9 +42,9 @@ FLOP_PER_PAIR = 22
 
 
 # DRAM bytes of one launch of the dominant kernel (dram__bytes_read.sum +
-# dram__bytes_write.sum of k_cluster, 92,224-atom lattice) from the ncu capture
-# summarised in profiles/k_cluster_lattice92k.md, with the SHA-256 of the kernel's
-# sources it was taken on: the figure is reported as null once they have changed.
+# dram__bytes_write.sum of k_cluster, 92,224-atom lattice) from one ncu capture, with
+# the SHA-256 of the kernel's sources it was taken on: the figure is reported as null
+# once they have changed.
 TRAFFIC_CAPTURE = {"bytes": 3362304, "atoms": 92224,
                    "kernel_source_sha256": "f7e3af0e7f095a588105ad934e768c07d032a775a7246fe0573cc02e34b3160f"}
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1611_04474_gb300", "csrc", f)
@@ -248,6 +250,22 @@ def measure_energy(eng, stream, dev_index: int, seconds: float = 2.0, dt_fs: flo
             "dt_fs": dt_fs, "source": "nvidia-smi power.draw, 50 ms samples within the run"}
 
 
+def measure_peak(dev_index: int):
+    """The FP32 multiply-add peak of this GPU (paper_1611_04474_gb300.peak), with the SM
+    clock sampled while the probe runs."""
+    from paper_1611_04474_gb300 import peak
+
+    clocks = ClockSampler(dev_index)
+    clocks.path = clocks.path.replace("clocks_gpu", "clocks_peak_gpu")
+    clocks.start()
+    time.sleep(0.3)
+    out = peak.measure_fp32_peak()
+    clk = clocks.stop()
+    out["sm_mhz"] = clk.get("sm_mhz")
+    out["reasons"] = clk.get("reasons")
+    return out
+
+
 def combine_ranks(pairs: float, step_ms: float, e2e_ms: float, device=None):
     """Whole-job figures over the ranks of a replica run: the pairs all ranks processed,
     and the slowest rank's device time (max over ranks).  Works on any initialised
@@ -273,6 +291,39 @@ def bench_config(s, args, world: int) -> dict:
             "accum": args.mode, "algo": args.algo, "dt_fs": args.dt,
             "l2": "flushed (256 MB write) before every timed step",
             "parallelism": f"replicas x{world}"}
+
+
+def cpu_oracle_whole(s, gpu_forces=None):
+    """The FP64 oracle as it stands, single-threaded: one whole-system evaluation
+    (orc_forces_cells, Algorithm 1 over every cell).  Returns (pairs/s, seconds, accuracy
+    of gpu_forces against it on every atom, or None)."""
+    import oracle
+
+    ff = oracle.ForceField.from_system(s)
+    p = s.pos.astype(np.float64)
+    t0 = time.perf_counter()
+    ref = oracle.forces_cells(p, s.q, s.type, s.box, ff)
+    dt = time.perf_counter() - t0
+    acc = None
+    if gpu_forces is not None:
+        # atoms with a pair whose FP64 r^2 lies within 16 float32 ulps of rc^2 may see that
+        # pair kept by one side and dropped by the other; both are correct roundings, so
+        # those atoms are left out of the figures (the tests check them separately)
+        ij, _ = oracle.boundary_pairs(p, s.box, s.rc, 16 * 2.0**-24 * s.rc * s.rc)
+        use = np.ones(s.n, dtype=bool)
+        use[ij.ravel()] = False
+        dF = np.linalg.norm(gpu_forces - ref.F, axis=1)[use]
+        nF = np.linalg.norm(ref.F, axis=1)[use]
+        raw = dF / np.maximum(nF, 1e-300)
+        worst = int(np.argmax(raw))
+        acc = {"atoms_checked": int(use.sum()), "boundary_atoms_excluded": int((~use).sum()),
+               "max_err_over_term_sum": float((dF / ref.cond[use]).max()),
+               "max_rel_err": float(raw.max()),
+               "max_rel_err_atom": {"abs_F": float(nF[worst]), "term_sum": float(ref.cond[use][worst]),
+                                    "abs_dF": float(dF[worst])},
+               "rms_rel_err": float(np.sqrt((dF**2).sum() / (nF**2).sum())),
+               "oracle": "orc_forces_cells, whole system"}
+    return ref.npairs / dt, dt, acc
 
 
 def cpu_oracle_rate(s, seconds: float, seed: int = 0, gpu_forces=None):
@@ -411,6 +462,7 @@ def run_ours(args):
     status = int(eng.status.item())
     clk = clocks.stop()
     energy = None if args.no_energy else measure_energy(eng, stream, dev.index)
+    fp32_peak = measure_peak(dev.index)
 
     # end to end through the public API with host buffers: the step's state (positions,
     # velocities, forces) lives in one pinned host buffer and one device buffer, so that
@@ -454,8 +506,8 @@ def run_ours(args):
     if energy:
         energy["pairs_per_joule"] = pairs_per_step / energy["joules_per_step"]
     flops = FLOP_PER_CANDIDATE * candidates + FLOP_PER_PAIR * pairs_end
-    sm_clock_ghz = 2.07
-    peak_tflops = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_clock_ghz / 1e3
+    nominal_tflops = NOMINAL_SMS * FP32_LANES_PER_SM * 2 * NOMINAL_SM_GHZ / 1e3
+    peak_tflops = fp32_peak["tflops"]
     achieved = flops / (t_force / 1e3) / 1e12
     # per MD step: kick + drift + wrap + cell index and bin (+ scan of the cell counts in
     # its last block), cell sort into cluster order, force kernel, finalize + kick
@@ -474,7 +526,16 @@ def run_ours(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops, "traffic": captured_traffic(s.n),
                      "kernel": "md_nonbonded_forces",
-                     "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz (derived)"},
+                     "flop_per_eval": flops,
+                     "work": f"{FLOP_PER_CANDIDATE} FLOP x {candidates} half-shell candidates + "
+                             f"{FLOP_PER_PAIR} FLOP x {pairs_end} pairs, over the mean "
+                             f"event-timed force call of {t_force:.5f} ms",
+                     "peak_basis": "measured: FP32 multiply-add probe (best of FFMA and FFMA2, "
+                                   f"{fp32_peak['sms']} SMs, median SM clock "
+                                   f"{fp32_peak.get('sm_mhz')} MHz during the probe)",
+                     "nominal_peak": nominal_tflops,
+                     "frac_of_nominal": achieved / nominal_tflops},
+        "fp32_peak": fp32_peak,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps * per_step_launches,
@@ -483,9 +544,18 @@ def run_ours(args):
         "status": status,
     }
     if rank == 0 and not args.no_cpu_baseline:
-        rate, sample, acc = cpu_oracle_rate(s, args.cpu_seconds, gpu_forces=forces_start)
+        from paper_1611_04474_gb300 import workloads as W
+
+        rate, secs, acc = cpu_oracle_whole(s, gpu_forces=forces_start)
+        sweep = []
+        for small in (W.workload_random_3000(), workload(23056)):
+            r, t, _ = cpu_oracle_whole(small)
+            sweep.append({"atoms": small.n, "seconds": t, "pairs_per_s": r})
+        srate, sample, _ = cpu_oracle_rate(s, 3.0)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": sample}
+                                "sample": f"one whole-system evaluation of the {s.n}-atom workload "
+                                          f"(orc_forces_cells, FP64, single thread, {secs:.1f} s)",
+                                "sweep": sweep, "sampled_atoms": {"value": srate, "sample": sample}}
         # the same oracle forces also check the GPU's forces of the starting state
         line["accuracy_vs_oracle"] = acc
     if world > 1:

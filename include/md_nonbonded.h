@@ -149,7 +149,11 @@ int md_build_cells(const float *pos_q, const int32_t *type, int32_t n, const dou
  *   else MD_ERR_TOO_LARGE and nothing is enqueued.  Every GPU that loads the library
  *   holds MD_NOALLOC_SCRATCH_BYTES for this array until the process exits.
  *   The first call on each device looks up the array's device address on that device
- *   (the current one); make that first call before any stream capture begins.
+ *   (the current one) and keeps it for the life of the process; make that first call
+ *   before any stream capture begins.  The kept address is not valid after the device is
+ *   reset (cudaDeviceReset, or a runtime that tears down the primary context): the module
+ *   is loaded again and may land elsewhere, so do not call this entry point after such
+ *   a reset in the same process.
  *   All calls on a device share the array and it keeps the last call's contents (the
  *   counters are cleared on every call).  Calls that overlap on the GPU race on it and
  *   give wrong cell lists: issue them in order on one stream.

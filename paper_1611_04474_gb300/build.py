@@ -18,6 +18,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(ROOT, "_build")
 LIB_PATH = os.path.join(HERE, "libmdnb.so")
+# measurement support (FP32 peak probe), kept out of the product library
+PROBE_SRC = os.path.join(HERE, "csrc_probe", "fp32_peak.cu")
+PROBE_PATH = os.path.join(HERE, "libmdprobe.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -78,7 +81,21 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
         os.replace(tmp, LIB_PATH)
+    build_probe(force)
     return LIB_PATH
+
+
+def build_probe(force: bool = False) -> str:
+    """libmdprobe.so: the FP32 multiply-add throughput probe the benchmark's roofline uses."""
+    if force or _stale(PROBE_PATH, [PROBE_SRC]):
+        tmp = PROBE_PATH + f".tmp{os.getpid()}"
+        cmd = [nvcc_path(), *ARCH, "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
+               "--cudart", "shared", "-o", tmp, PROBE_SRC, "-Xlinker", "-rpath=/usr/local/cuda/lib64"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed on {PROBE_SRC}:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, PROBE_PATH)
+    return PROBE_PATH
 
 
 if __name__ == "__main__":

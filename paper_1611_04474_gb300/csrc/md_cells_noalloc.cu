@@ -36,7 +36,9 @@ constexpr int kMaxDevices = 64;
 std::mutex g_addr_mutex;
 void *g_addr[kMaxDevices] = {};
 
-// Device address of the scratch on the current device, looked up once per device.
+// Device address of the scratch on the current device, looked up once per device and
+// kept for the life of the process (not valid after a device reset, which reloads the
+// module; the header says so).
 cudaError_t scratch_address(void **out)
 {
     int dev = 0;

@@ -64,6 +64,39 @@ def test_noalloc_cell_build_matches_workspace_entry_point(cuda_lib):
         assert int(st_a.item()) == int(st_b.item()) == 0
 
 
+def _uniform(n, box, seed):
+    rng = np.random.default_rng(seed)
+    box = np.asarray(box, dtype=np.float64)
+    pos = W.to_f32_in_box(rng.uniform(0.0, 1.0, (n, 3)) * box, box)
+    pos_q = np.concatenate([pos, rng.uniform(-1, 1, (n, 1)).astype(np.float32)], axis=1)
+    return pos_q, rng.integers(0, 4, n).astype(np.int32), box
+
+
+def test_noalloc_at_its_limits(cuda_lib):
+    """The most atoms and cells the scratch holds: 131,072 atoms over 32 x 32 x 16 = 16,384
+    cells fills the array to its last byte and takes the global-histogram path (more than
+    8,192 cells); then 131,072 atoms over a small grid (the shared-memory histogram)."""
+    api = cuda_lib
+    lib = _lib(api)
+    cases = [(MAX_ATOMS, (64.0, 64.0, 32.0), 1.99, (32, 32, 16)),
+             (MAX_ATOMS, (60.0, 61.0, 62.5), 7.5, (8, 8, 8))]
+    for k, (n, box, rc, want) in enumerate(cases):
+        pos_q_np, types_np, box64 = _uniform(n, box, seed=k)
+        dims = api.cell_dims(box, rc)
+        assert tuple(dims) == want
+        pos_q = torch.as_tensor(pos_q_np).cuda()
+        types = torch.as_tensor(types_np).cuda()
+        st_a = torch.zeros(1, dtype=torch.int32, device="cuda")
+        st_b = torch.zeros(1, dtype=torch.int32, device="cuda")
+        got = _noalloc(api, lib, pos_q, types, list(box), dims, st_a)
+        ws = api.make_workspace(n, dims)
+        ref = api.build_cells(pos_q, types, list(box), dims, ws, status=st_b)
+        torch.cuda.synchronize()
+        for name in ("cell_start", "perm", "pos_q_sorted", "type_sorted"):
+            assert np.array_equal(getattr(got, name).cpu().numpy(), getattr(ref, name).cpu().numpy()), (k, name)
+        assert int(st_a.item()) == int(st_b.item()) == 0
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch(cuda_lib):
     api = cuda_lib
     lib = _lib(api)
