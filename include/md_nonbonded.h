@@ -223,6 +223,34 @@ int md_step(double *pos, double *vel, void *forces, int32_t forces_valid, const 
             void *stream);
 
 /*
+ * md_step_verlet -- md_step with a Verlet skin: the cells are built with edge >= rc + skin
+ * and kept, with the order of the atoms within them, while no atom has moved skin/2 or
+ * more since they were built; then they are built again (Section II.A's cell method,
+ * reused across steps).  Every pair closer than rc lies in neighbouring kept cells, so the
+ * forces are those of md_step: in MD_ACCUM_FIXED64 the same bits, step for step, and in
+ * MD_ACCUM_F32 the same up to the order of summation.  The force kernel reads the current
+ * positions through the kept order and filters cluster pairs on their current boxes; an
+ * atom that crosses a face of the box while the cells are kept is handled by the
+ * per-pair minimum image.  The rebuild decision is taken on the device (no host
+ * synchronisation): each step measures the largest move since the last build, and the
+ * rebuild kernels return at once when none is needed.
+ *   skin          A, > 0, with rc + skin < min(L)/2 (else MD_ERR_CUTOFF)
+ *   mode          MD_ACCUM_F32, MD_ACCUM_FIXED64 or MD_ACCUM_FIXED_TILE
+ *   rebuilds      device uint64[1] or NULL: the number of cell builds is added to it
+ *   workspace     md_verlet_workspace_bytes(n, box_L, ff->rc, skin) bytes.  The kept
+ *                 cells live in it only for the duration of one call: the first step of
+ *                 every call builds them.
+ * Other arguments, outputs and status bits as md_step.
+ */
+size_t md_verlet_workspace_bytes(int32_t n, const double *box_L, double rc, double skin);
+int md_step_verlet(double *pos, double *vel, void *forces, int32_t forces_valid,
+                   const float *inv_mass, const float *q, const int32_t *type, int32_t n,
+                   const double *box_L, const md_forcefield *ff, int32_t mode, double dt_fs,
+                   int32_t n_steps, double skin, double *energy_log,
+                   unsigned long long *rebuilds, void *workspace, size_t ws_bytes,
+                   uint32_t *status, void *stream);
+
+/*
  * Batches of independent systems (many small MD problems advanced together; the
  * paper's method applied to each system independently).
  *

@@ -32,6 +32,7 @@ FIXED_SCALE = 2.0**32
 
 EXPORTS = ("md_strerror", "md_abi_version", "md_cell_dims", "md_workspace_bytes", "md_build_cells",
            "md_build_cells_noalloc", "md_nonbonded_forces", "md_nonbonded_forces_algo", "md_step",
+           "md_verlet_workspace_bytes", "md_step_verlet",
            "md_batch_workspace_bytes", "md_batch_prepare", "md_batch_step", "md_batch_step_tuned")
 BATCH_SHAPES = 6  # MD_BATCH_SHAPES: kernel shapes of the batched force launches
 
@@ -86,6 +87,11 @@ def load(path: str | None = None):
     lib.md_nonbonded_forces_algo.restype = ctypes.c_int
     lib.md_step.argtypes = [P, P, P, i32, P, P, P, i32, P, P, i32, f64, i32, P, P, sz, P, P]
     lib.md_step.restype = ctypes.c_int
+    lib.md_verlet_workspace_bytes.argtypes = [i32, P, f64, f64]
+    lib.md_verlet_workspace_bytes.restype = sz
+    lib.md_step_verlet.argtypes = [P, P, P, i32, P, P, P, i32, P, P, i32, f64, i32, f64, P, P, P, sz,
+                                   P, P]
+    lib.md_step_verlet.restype = ctypes.c_int
     lib.md_batch_workspace_bytes.argtypes = [i32, P]
     lib.md_batch_workspace_bytes.restype = sz
     lib.md_batch_prepare.argtypes = [i32, P, P, sz, P]
@@ -257,6 +263,39 @@ def step(pos, vel, forces, forces_valid: bool, inv_mass, q, types, box, ff: Forc
         _ptr(workspace), workspace.numel(), _ptr(status), _stream(stream)))
 
 
+def verlet_workspace_bytes(n: int, box, rc: float, skin: float) -> int:
+    b = int(load().md_verlet_workspace_bytes(int(n), _box(box), float(rc), float(skin)))
+    if b == 0:
+        raise ValueError("invalid n, box, cutoff or skin (rc + skin must stay below min(L)/2)")
+    return b
+
+
+def step_verlet(pos, vel, forces, forces_valid: bool, inv_mass, q, types, box, ff: ForceField,
+                mode, dt_fs: float, n_steps: int, skin: float, workspace, energy_log=None,
+                rebuilds=None, status=None, stream=None):
+    """md_step_verlet: n_steps of velocity Verlet with cells kept while every atom stays
+    within skin/2 of where it was when they were built."""
+    n = int(pos.shape[0])
+    _need(pos, torch.float64, (n, 3), "pos")
+    _need(vel, torch.float64, (n, 3), "vel")
+    _need(forces, FORCE_DTYPE[mode], (n, 3), "forces")
+    _need(inv_mass, torch.float32, (n,), "inv_mass")
+    _need(q, torch.float32, (n,), "q")
+    _need(types, torch.int32, (n,), "types")
+    _need(workspace, torch.uint8, None, "workspace")
+    if energy_log is not None:
+        _need(energy_log, torch.float64, (n_steps, 4), "energy_log")
+    if rebuilds is not None:
+        _need(rebuilds, torch.int64, (1,), "rebuilds")
+    if status is not None:
+        _need(status, torch.int32, (1,), "status")
+    _check("md_step_verlet", load().md_step_verlet(
+        _ptr(pos), _ptr(vel), _ptr(forces), int(bool(forces_valid)), _ptr(inv_mass), _ptr(q),
+        _ptr(types), n, _box(box), ff.c, int(mode), float(dt_fs), int(n_steps), float(skin),
+        _ptr(energy_log), _ptr(rebuilds), _ptr(workspace), workspace.numel(), _ptr(status),
+        _stream(stream)))
+
+
 def forces_to_f64(F: torch.Tensor, mode: int) -> torch.Tensor:
     """Forces of any mode as float64 kcal/mol/A."""
     if mode in (ACCUM_FIXED64, ACCUM_FIXED_TILE):
@@ -305,6 +344,20 @@ class Engine:
         step(self.pos, self.vel, self.forces, self.forces_valid, self.inv_mass, self.q,
              self.types, self.box, self.ff, self.mode, dt_fs, n_steps, self.workspace,
              energy_log=energy_log, status=self.status, stream=stream)
+        self.forces_valid = True
+
+    def step_verlet(self, n_steps=1, dt_fs=1.0, skin=1.0, energy_log=None, stream=None):
+        """md_step_verlet on this system's state; the number of cell builds accumulates in
+        self.rebuilds (a device int64[1])."""
+        need = verlet_workspace_bytes(self.n, self.box, self.ff.rc, skin)
+        if getattr(self, "verlet_ws", None) is None or self.verlet_ws.numel() < need:
+            self.verlet_ws = torch.empty(need, dtype=torch.uint8, device=self.pos.device)
+        if getattr(self, "rebuilds", None) is None:
+            self.rebuilds = torch.zeros(1, dtype=torch.int64, device=self.pos.device)
+        step_verlet(self.pos, self.vel, self.forces, self.forces_valid, self.inv_mass, self.q,
+                    self.types, self.box, self.ff, self.mode, dt_fs, n_steps, skin, self.verlet_ws,
+                    energy_log=energy_log, rebuilds=self.rebuilds, status=self.status,
+                    stream=stream)
         self.forces_valid = True
 
 

@@ -107,7 +107,7 @@ int bin_capacity(int n, int ncell)
     return (int)(cap < (1LL << 30) ? cap : (1LL << 30));
 }
 
-WsLayout ws_layout(int n, int ncell, bool bins)
+WsLayout ws_layout(int n, int ncell, bool bins, bool verlet)
 {
     WsLayout w;
     size_t nn = (size_t)(n > 0 ? n : 1);
@@ -135,6 +135,8 @@ WsLayout ws_layout(int n, int ncell, bool bins)
     w.work = off;            off = align_up(off + 2 * sizeof(int32_t));
     w.bin_cap = bins && n > 0 ? bin_capacity(n, (int)nc) : 0;
     w.bins = off;            off = align_up(off + sizeof(int32_t) * nc * (size_t)w.bin_cap);
+    w.v_ref = off;           off = align_up(off + (verlet ? sizeof(float4) * nn : 0));
+    w.v_flags = off;         off = align_up(off + (verlet ? sizeof(VerletFlags) : 0));
     w.total = off;
     return w;
 }
@@ -371,6 +373,109 @@ int md_step(double *pos, double *vel, void *forces, int32_t forces_valid, const 
         if ((ce = eval_forces(energy_log != nullptr, true)) != cudaSuccess) return MD_ERR_CUDA;
         if (energy_log) {
             ce = launch_energy_log_row(vel, inv_mass, n, ev, energy_log + 4 * (size_t)st, ws, wsp, s);
+            if (ce != cudaSuccess) return MD_ERR_CUDA;
+        }
+    }
+    return MD_OK;
+}
+
+size_t md_verlet_workspace_bytes(int32_t n, const double *box_L, double rc, double skin)
+{
+    int32_t dims[3];
+    if (n < 0 || n > kMaxAtoms || !(skin > 0.0) || !isfinite(skin)) return 0;
+    if (compute_dims(box_L, rc + skin, dims) != MD_OK) return 0;
+    return ws_layout(n, dims[0] * dims[1] * dims[2], false, true).total + kAlign;
+}
+
+int md_step_verlet(double *pos, double *vel, void *forces, int32_t forces_valid,
+                   const float *inv_mass, const float *q, const int32_t *type, int32_t n,
+                   const double *box_L, const md_forcefield *ff, int32_t mode, double dt_fs,
+                   int32_t n_steps, double skin, double *energy_log,
+                   unsigned long long *rebuilds, void *workspace, size_t ws_bytes,
+                   uint32_t *status, void *stream)
+{
+    if (n < 0 || n > kMaxAtoms || n_steps < 0) return MD_ERR_INVALID_ARG;
+    if (!(dt_fs > 0.0) || !isfinite(dt_fs)) return MD_ERR_INVALID_ARG;
+    if (!(skin > 0.0) || !isfinite(skin)) return MD_ERR_INVALID_ARG;
+    int e = check_ff(ff);
+    if (e) return e;
+    if (mode != MD_ACCUM_F32 && mode != MD_ACCUM_FIXED64 && mode != MD_ACCUM_FIXED_TILE)
+        return MD_ERR_INVALID_ARG;
+    int32_t dims[3];
+    if ((e = compute_dims(box_L, ff->rc, dims))) return e;       // rc itself
+    if ((e = compute_dims(box_L, ff->rc + skin, dims))) return e;  // the Verlet grid
+    if (n > 0 && (!pos || !vel || !forces || !inv_mass || !q || !type)) return MD_ERR_INVALID_ARG;
+    const int ncell = dims[0] * dims[1] * dims[2];
+    WsLayout ws = ws_layout(n, ncell, false, true);
+    char *wsp = ws_base(workspace, ws_bytes, ws);
+    if (!wsp) return MD_ERR_WORKSPACE;
+    if (n == 0 || (n_steps == 0 && forces_valid)) return MD_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    BoxF box = make_box(box_L, dims);
+    int32_t *cs = reinterpret_cast<int32_t *>(wsp + ws.st_cell_start);
+    int32_t *pm = reinterpret_cast<int32_t *>(wsp + ws.st_perm);
+    float4 *pqs = reinterpret_cast<float4 *>(wsp + ws.st_pos_q_sorted);
+    int32_t *tys = reinterpret_cast<int32_t *>(wsp + ws.st_type_sorted);
+    float4 *pq = reinterpret_cast<float4 *>(wsp + ws.st_pos_q);
+    float4 *x_ref = reinterpret_cast<float4 *>(wsp + ws.v_ref);
+    VerletFlags *flags = reinterpret_cast<VerletFlags *>(wsp + ws.v_flags);
+    double *ev = reinterpret_cast<double *>(wsp + ws.ev);
+    void *accum = wsp + ws.accum;
+    // rebuild when an atom has moved s/2 or more since the cells were built (less a
+    // margin for the float rounding of the positions the move is measured on)
+    const double lmax = fmax(box_L[0], fmax(box_L[1], box_L[2]));
+    const double half_skin = 0.5 * skin - 4.0 * 1.1920929e-7 * lmax;  // a few float ulps of L
+    const float threshold2 = half_skin > 0.0 ? (float)(half_skin * half_skin) : 0.0f;
+
+    ForceArgs a;
+    a.cell_start = cs;
+    a.perm = pm;
+    a.pos_q_sorted = pqs;
+    a.type_sorted = tys;
+    a.n = n;
+    a.box = box;
+    a.AB = reinterpret_cast<const float2 *>(ff->AB);
+    a.ntypes = ff->ntypes;
+    a.k_coulomb = (float)ff->k_coulomb;
+    a.k_coulomb64 = ff->k_coulomb;
+    a.rc = (float)ff->rc;
+    a.rc64 = ff->rc;
+    a.mode = mode;
+    a.algo = MD_ALGO_CLUSTER;
+    a.forces_out = forces;
+    a.pair_count_out = nullptr;
+    a.status = status;
+    a.presorted = 1;
+    a.accum_zeroed = 1;  // the drift pass zeroes the accumulators
+    a.gather_pq = pq;
+    a.kick_inv_mass = inv_mass;
+    const double half_dt = 0.5 * dt_fs;
+    a.kick_half_dt = half_dt;
+    const int *run = &flags->rebuild;
+    // every step's passes: [half kick +] drift + wrap + float copy + largest move, the
+    // rebuild decision, the rebuild kernels (which return at once without one), the forces
+    // through the kept cells and the second half kick; the first step of a call rebuilds
+    auto step = [&](bool kick, double dt, bool first, bool energy, bool kick2) -> cudaError_t {
+        cudaError_t ce = launch_verlet_drift(pos, vel, forces, mode, inv_mass, q, n, box, dt, half_dt,
+                                             kick, pq, x_ref, accum, flags, status, s);
+        if (ce == cudaSuccess) ce = launch_verlet_decide(flags, threshold2, first, rebuilds, s);
+        if (ce == cudaSuccess)
+            ce = launch_verlet_rebuild(pq, type, n, box, cs, pm, pqs, tys, x_ref, run, ws, wsp, status, s);
+        if (ce != cudaSuccess) return ce;
+        a.energy_virial_out = energy ? ev : nullptr;
+        a.kick_vel = kick2 ? vel : nullptr;
+        return launch_forces(a, ws, wsp, s);
+    };
+    bool first = true;
+    if (!forces_valid) {
+        if (step(false, 0.0, true, false, false) != cudaSuccess) return MD_ERR_CUDA;
+        first = false;
+    }
+    for (int st = 0; st < n_steps; ++st) {
+        if (step(true, dt_fs, first, energy_log != nullptr, true) != cudaSuccess) return MD_ERR_CUDA;
+        first = false;
+        if (energy_log) {
+            cudaError_t ce = launch_energy_log_row(vel, inv_mass, n, ev, energy_log + 4 * (size_t)st, ws, wsp, s);
             if (ce != cudaSuccess) return MD_ERR_CUDA;
         }
     }

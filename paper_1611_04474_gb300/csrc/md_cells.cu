@@ -31,9 +31,10 @@ constexpr int kSortChunk = 2048;  // members staged in shared memory at a time
 template <bool SMEM>
 __global__ void __launch_bounds__(kIndexThreads)
 k_cell_index(const float4 *__restrict__ pos_q, int n, BoxF box, int *__restrict__ cell_id,
-             int *__restrict__ cell_cnt, uint32_t *status)
+             int *__restrict__ cell_cnt, uint32_t *status, const int *__restrict__ run_flag)
 {
     extern __shared__ int s_hist[];
+    if (run_flag && !*run_flag) return;  // Verlet step without a rebuild
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int ncell = box.ncell;
     if (SMEM) {
@@ -64,9 +65,11 @@ k_cell_index(const float4 *__restrict__ pos_q, int n, BoxF box, int *__restrict_
 // Single block: exclusive scan of the per-cell counts.  Writes cell_start[0..ncell]
 // and turns the counts into scatter cursors (= cell_start[c]).
 __global__ void __launch_bounds__(kScanThreads)
-k_scan_cells(int *__restrict__ cnt_cursor, int ncell, int *__restrict__ cell_start)
+k_scan_cells(int *__restrict__ cnt_cursor, int ncell, int *__restrict__ cell_start,
+             const int *__restrict__ run_flag)
 {
     __shared__ int sums[kScanThreads];
+    if (run_flag && !*run_flag) return;
     int t = threadIdx.x;
     int per = (ncell + kScanThreads - 1) / kScanThreads;
     int lo = min(t * per, ncell), hi = min(lo + per, ncell);
@@ -93,8 +96,10 @@ k_scan_cells(int *__restrict__ cnt_cursor, int ncell, int *__restrict__ cell_sta
 // Each atom takes a slot of its cell; the atoms of a warp that share a cell take
 // consecutive slots with one atomic (the order is fixed later by k_cell_sort).
 __global__ void __launch_bounds__(kIndexThreads)
-k_scatter(const int *__restrict__ cell_id, int n, int *__restrict__ cursor, int *__restrict__ perm_tmp)
+k_scatter(const int *__restrict__ cell_id, int n, int *__restrict__ cursor, int *__restrict__ perm_tmp,
+          const int *__restrict__ run_flag)
 {
+    if (run_flag && !*run_flag) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const int c = i < n ? cell_id[i] : -1;
@@ -331,7 +336,8 @@ k_sort_cluster(int *__restrict__ cell_start, const int *__restrict__ perm_tmp,
                const int *__restrict__ counts, int ncell,
                const float4 *__restrict__ pos_q, const int32_t *__restrict__ type, BoxF box_in,
                BatchArgs b, int32_t *__restrict__ perm, float4 *__restrict__ pos_q_sorted,
-               int32_t *__restrict__ type_sorted)
+               int32_t *__restrict__ type_sorted, const int *__restrict__ run_flag,
+               float4 *__restrict__ x_ref)
 {
     __shared__ unsigned long long s_key[kClusterSortMax];  // by arrival
     __shared__ unsigned long long s_bkt[kClusterSortMax];  // grouped by column
@@ -342,9 +348,16 @@ k_sort_cluster(int *__restrict__ cell_start, const int *__restrict__ perm_tmp,
     __shared__ int s_typ[kClusterSortMax];     // types, by arrival
     pdl_wait();
     pdl_trigger();
+    if (run_flag && !*run_flag) return;  // Verlet step without a rebuild
     const int cg = blockIdx.x;
     const BoxF &box = BATCHED ? b.sys[b.cell_sys[cg]].box : box_in;
     const int c = BATCHED ? cg - b.sys[b.cell_sys[cg]].cell_offset : cg;
+    // Verlet step: each member's position at this rebuild (input order), from what
+    // place() or the staged copy writes
+    auto put = [&](int e, int slot) {
+        place(e, slot, pos_q, type, box, perm, pos_q_sorted, type_sorted);
+        if (x_ref) x_ref[e] = pos_q_sorted[slot];
+    };
     int s0, m;
     if (counts) {
         // this cell's start from the counts of the cells before it (a block sum), and
@@ -391,7 +404,7 @@ k_sort_cluster(int *__restrict__ cell_start, const int *__restrict__ perm_tmp,
             const int pos = before + __popc(bal & ((1u << lane) - 1u));
             if (mine && pos < m) {
                 if (m > kClusterSortMax)
-                    place(j, s0 + pos, pos_q, type, box, perm, pos_q_sorted, type_sorted);
+                    put(j, s0 + pos);
                 else
                     list[pos] = j;
             }
@@ -415,7 +428,7 @@ k_sort_cluster(int *__restrict__ cell_start, const int *__restrict__ perm_tmp,
                 __syncthreads();
                 for (int u = 0; u < len; ++u) rank += chunk[u] < e;
             }
-            if (e >= 0) place(e, s0 + rank, pos_q, type, box, perm, pos_q_sorted, type_sorted);
+            if (e >= 0) put(e, s0 + rank);
         }
         return;
     }
@@ -473,9 +486,11 @@ k_sort_cluster(int *__restrict__ cell_start, const int *__restrict__ perm_tmp,
         for (int u = b0; u < b1; ++u) rank += s_bkt[u] < key;
         // what place() writes, from the copies staged above
         const int slot = s0 + b0 + rank;
-        perm[slot] = (int)(key & ((1ull << 30) - 1));
+        const int e = (int)(key & ((1ull << 30) - 1));
+        perm[slot] = e;
         pos_q_sorted[slot] = s_pos[t];
         type_sorted[slot] = s_typ[t];
+        if (x_ref) x_ref[e] = s_pos[t];
     }
 }
 
@@ -494,14 +509,14 @@ cudaError_t launch_build_cells(const float4 *pos_q, const int32_t *type, int n, 
     if (n > 0) {
         int g = (n + kIndexThreads - 1) / kIndexThreads;
         if (box.ncell <= kSmemCells)
-            k_cell_index<true><<<g, kIndexThreads, sizeof(int) * box.ncell, stream>>>(pos_q, n, box, cell_id, cnt, status);
+            k_cell_index<true><<<g, kIndexThreads, sizeof(int) * box.ncell, stream>>>(pos_q, n, box, cell_id, cnt, status, nullptr);
         else
-            k_cell_index<false><<<g, kIndexThreads, 0, stream>>>(pos_q, n, box, cell_id, cnt, status);
+            k_cell_index<false><<<g, kIndexThreads, 0, stream>>>(pos_q, n, box, cell_id, cnt, status, nullptr);
     }
-    k_scan_cells<<<1, kScanThreads, 0, stream>>>(cnt, box.ncell, cell_start);
+    k_scan_cells<<<1, kScanThreads, 0, stream>>>(cnt, box.ncell, cell_start, nullptr);
     if (n > 0) {
         int g = (n + kIndexThreads - 1) / kIndexThreads;
-        k_scatter<<<g, kIndexThreads, 0, stream>>>(cell_id, n, cnt, perm_tmp);
+        k_scatter<<<g, kIndexThreads, 0, stream>>>(cell_id, n, cnt, perm_tmp, nullptr);
         k_cell_sort<<<box.ncell, kSortThreads, 0, stream>>>(cell_start, perm_tmp, pos_q, type, box, perm,
                                                              pos_q_sorted, type_sorted);
     }
@@ -548,20 +563,50 @@ cudaError_t launch_kick_drift_build(double *pos, double *vel, const void *forces
     // the shared-histogram form scans in its last block (without bins) or in the cell
     // sort (with bins)
     const bool sort_scans = n > 0 && sm && cap;
-    if (n == 0 || !sm) k_scan_cells<<<1, kScanThreads, 0, stream>>>(cnt, ncell, cell_start);
+    if (n == 0 || !sm) k_scan_cells<<<1, kScanThreads, 0, stream>>>(cnt, ncell, cell_start, nullptr);
     if (n > 0) {
         // with bins the members are already grouped by cell
         if (!cap) {
             const int g = (n + kIndexThreads - 1) / kIndexThreads;
-            k_scatter<<<g, kIndexThreads, 0, stream>>>(cell_id, n, cnt, perm_tmp);
+            k_scatter<<<g, kIndexThreads, 0, stream>>>(cell_id, n, cnt, perm_tmp, nullptr);
         }
         // after the scatter, or straight after the build pass (programmatic launch)
         if (b)
-            e = launch_pdl(k_sort_cluster<true>, dim3(ncell), dim3(kSortThreads), 0, stream, cell_start, perm_tmp, bins, cap, (const int *)cell_id, n, sort_scans ? (const int *)cnt : nullptr, ncell, (const float4 *)pos_q, type, box_in, bb, perm, pos_q_sorted, type_sorted);
+            e = launch_pdl(k_sort_cluster<true>, dim3(ncell), dim3(kSortThreads), 0, stream, cell_start, perm_tmp, bins, cap, (const int *)cell_id, n, sort_scans ? (const int *)cnt : nullptr, ncell, (const float4 *)pos_q, type, box_in, bb, perm, pos_q_sorted, type_sorted, (const int *)nullptr, (float4 *)nullptr);
         else
-            e = launch_pdl(k_sort_cluster<false>, dim3(ncell), dim3(kSortThreads), 0, stream, cell_start, perm_tmp, bins, cap, (const int *)cell_id, n, sort_scans ? (const int *)cnt : nullptr, ncell, (const float4 *)pos_q, type, box_in, bb, perm, pos_q_sorted, type_sorted);
+            e = launch_pdl(k_sort_cluster<false>, dim3(ncell), dim3(kSortThreads), 0, stream, cell_start, perm_tmp, bins, cap, (const int *)cell_id, n, sort_scans ? (const int *)cnt : nullptr, ncell, (const float4 *)pos_q, type, box_in, bb, perm, pos_q_sorted, type_sorted, (const int *)nullptr, (float4 *)nullptr);
         if (e != cudaSuccess) return e;
     }
+    return cudaGetLastError();
+}
+
+// The cell rebuild of a Verlet step (md_step_verlet): the counting sort of the input-order
+// float positions into the cells of the Verlet grid, each cell's members straight into
+// cluster order, and x_ref[i] = the position each atom has at this rebuild.  Every kernel
+// reads *run_flag first and returns at once when it is 0 (no rebuild this step), so the
+// launches can be enqueued every step without a host decision.
+cudaError_t launch_verlet_rebuild(const float4 *pos_q, const int32_t *type, int n, const BoxF &box,
+                                  int32_t *cell_start, int32_t *perm, float4 *pos_q_sorted,
+                                  int32_t *type_sorted, float4 *x_ref, const int *run_flag,
+                                  const WsLayout &ws, char *wsp, uint32_t *status,
+                                  cudaStream_t stream)
+{
+    int *cell_id = reinterpret_cast<int *>(wsp + ws.cell_id);
+    int *cnt = reinterpret_cast<int *>(wsp + ws.cell_cnt);
+    int *perm_tmp = reinterpret_cast<int *>(wsp + ws.perm_tmp);
+    cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int) * ((size_t)box.ncell + 1), stream);
+    if (e != cudaSuccess || n <= 0) return e;
+    const int g = (n + kIndexThreads - 1) / kIndexThreads;
+    if (box.ncell <= kSmemCells)
+        k_cell_index<true><<<g, kIndexThreads, sizeof(int) * box.ncell, stream>>>(pos_q, n, box, cell_id, cnt, status, run_flag);
+    else
+        k_cell_index<false><<<g, kIndexThreads, 0, stream>>>(pos_q, n, box, cell_id, cnt, status, run_flag);
+    k_scan_cells<<<1, kScanThreads, 0, stream>>>(cnt, box.ncell, cell_start, run_flag);
+    k_scatter<<<g, kIndexThreads, 0, stream>>>(cell_id, n, cnt, perm_tmp, run_flag);
+    const BatchArgs nob = {};
+    k_sort_cluster<false><<<box.ncell, kSortThreads, 0, stream>>>(
+        cell_start, perm_tmp, (const int *)nullptr, 0, (const int *)cell_id, n, (const int *)nullptr,
+        box.ncell, pos_q, type, box, nob, perm, pos_q_sorted, type_sorted, run_flag, x_ref);
     return cudaGetLastError();
 }
 

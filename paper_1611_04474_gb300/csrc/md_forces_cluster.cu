@@ -187,6 +187,10 @@ struct CluArgs {
     int n;
     Partial *partials;
     uint32_t *status;
+    // Verlet step (GATHER): slot s holds atom perm[s]; its current position is gpq[perm[s]]
+    // (input order, wrapped in FP64 and rounded to float)
+    const float4 *gpq;
+    const int32_t *perm;
 };
 
 // Bounding boxes of the clusters of a staged tile (padding excluded).
@@ -229,6 +233,9 @@ struct CluSmem {
     Acc nf[NW][2 * kRow + kCTile];
     __device__ __forceinline__ Acc &react(int w, int d, int t) { return nf[w][d * kRow + t]; }
     int next;                   // next home cluster to hand out
+    // Verlet step: one bit per tile atom whose coordinate was wrapped across a face of
+    // the box since the cells were built (home and neighbour tile)
+    unsigned hwb[kCTile / 32], jwb[kCTile / 32];
 };
 
 struct CluConst {
@@ -236,16 +243,32 @@ struct CluConst {
     int n, hbase; // atoms; slot of the home tile's first atom
     float kc, rc2, rc2m;
     float lo[3];
+    float hs[3], ns[3];  // the cell pair's shifts of home and neighbour coordinates
     float L[3], Lhi[3], Llo[3], invL[3];  // per-pair minimum image (boxes with a 2-cell axis)
     int T;
     uint32_t *status;
 };
 
+// Verlet step: whether cluster c of a tile holds an atom wrapped since the cells were
+// built (the 8 bits of its atoms in the tile's mask).
+__device__ __forceinline__ bool wrapped_cluster(const unsigned *bits, int c)
+{
+    return ((bits[c >> 2] >> ((c & 3) * 8)) & 0xffu) != 0u;
+}
+__device__ __forceinline__ bool wrapped_atom(const unsigned *bits, int t)
+{
+    return ((bits[t >> 5] >> (t & 31)) & 1u) != 0u;
+}
+
 // Home cluster ic against every neighbour cluster of the staged tile in range.
 // DIAG: the neighbour tile is the home tile (pairs ia < ja only); SHIFT: the cell
 // pair has a remainder shift to add to the difference; MI: the per-pair minimum image
-// (boxes with an axis of 2 cells, unshifted tiles).
-template <int MODE, int STATS, bool DIAG, bool SHIFT, bool MI>
+// (boxes with an axis of 2 cells, unshifted tiles).  GATHER (Verlet step, boxes with >= 3
+// cells per axis): a cluster pair with an atom wrapped across a face of the box since the
+// cells were built passes the box filter and takes the per-pair minimum image of the
+// unshifted coordinates (staged + shift, exact), which for a pair within rc gives the
+// bits of the shifted difference the plain step forms from freshly built cells.
+template <int MODE, int STATS, bool DIAG, bool SHIFT, bool MI, bool GATHER = false>
 __device__ __forceinline__ void cluster_row(CluSmem<MODE> &sm, const float2 *s_ab,
                                             const CluConst &k, int ic, int njc, int mh, int warp,
                                             int lane, float &e_lj, float &e_c, float &vir,
@@ -255,6 +278,7 @@ __device__ __forceinline__ void cluster_row(CluSmem<MODE> &sm, const float2 *s_a
     const int il = lane & 3, jl = lane >> 2;
     const int ia0 = ic * kCS + il, ia1 = ia0 + 4;
     const float4 p0 = sm.hp[ia0], p1 = sm.hp[ia1];
+    const bool hrow_wr = GATHER && wrapped_cluster(sm.hwb, ic);
     const f2 xi = f2_make(p0.x, p1.x), yi = f2_make(p0.y, p1.y), zi = f2_make(p0.z, p1.z);
     const f2 qi = f2_make(p0.w, p1.w);
     const int t0 = sm.ht[ia0] * k.T, t1 = sm.ht[ia1] * k.T;
@@ -301,6 +325,8 @@ __device__ __forceinline__ void cluster_row(CluSmem<MODE> &sm, const float2 *s_a
                 const float gy = fmaxf(0.f, fmaxf(ib[1] - sm.jb[4][jt], sm.jb[1][jt] - ib[4]));
                 const float gz = fmaxf(0.f, fmaxf(ib[2] - sm.jb[5][jt], sm.jb[2][jt] - ib[5]));
                 in = gx * gx + gy * gy + gz * gz < k.rc2m;
+                // a cluster with a wrapped atom has no meaningful box here: always a candidate
+                if (GATHER && (hrow_wr || wrapped_cluster(sm.jwb, jt))) in = true;
             }
         }
         unsigned todo = __ballot_sync(0xffffffffu, in);
@@ -322,6 +348,25 @@ __device__ __forceinline__ void cluster_row(CluSmem<MODE> &sm, const float2 *s_a
                              min_image_f32(p1.y, pj.y, k.Lhi[1], k.Llo[1], k.invL[1]));
                 dz = f2_make(min_image_f32(p0.z, pj.z, k.Lhi[2], k.Llo[2], k.invL[2]),
                              min_image_f32(p1.z, pj.z, k.Lhi[2], k.Llo[2], k.invL[2]));
+            } else if (GATHER && (hrow_wr || wrapped_cluster(sm.jwb, jc))) {
+                // the unshifted coordinates: a wrapped atom was staged as it is, any
+                // other with the cell pair's shift subtracted (exactly), so adding it back
+                // restores the coordinate exactly
+                const bool w0 = wrapped_atom(sm.hwb, ia0), w1 = wrapped_atom(sm.hwb, ia1);
+                const bool wj = wrapped_atom(sm.jwb, ja);
+                float r0[3] = {p0.x, p0.y, p0.z}, r1[3] = {p1.x, p1.y, p1.z}, rj[3] = {pj.x, pj.y, pj.z};
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    if (!w0) r0[d] = __fadd_rn(r0[d], k.hs[d]);
+                    if (!w1) r1[d] = __fadd_rn(r1[d], k.hs[d]);
+                    if (!wj) rj[d] = __fadd_rn(rj[d], k.ns[d]);
+                }
+                dx = f2_make(min_image_f32(r0[0], rj[0], k.Lhi[0], k.Llo[0], k.invL[0]),
+                             min_image_f32(r1[0], rj[0], k.Lhi[0], k.Llo[0], k.invL[0]));
+                dy = f2_make(min_image_f32(r0[1], rj[1], k.Lhi[1], k.Llo[1], k.invL[1]),
+                             min_image_f32(r1[1], rj[1], k.Lhi[1], k.Llo[1], k.invL[1]));
+                dz = f2_make(min_image_f32(r0[2], rj[2], k.Lhi[2], k.Llo[2], k.invL[2]),
+                             min_image_f32(r1[2], rj[2], k.Lhi[2], k.Llo[2], k.invL[2]));
             } else {
                 dx = f2_sub(xi, f2_dup(pj.x));
                 dy = f2_sub(yi, f2_dup(pj.y));
@@ -465,8 +510,17 @@ __device__ __forceinline__ void cluster_row(CluSmem<MODE> &sm, const float2 *s_a
     }
 }
 
+// Verlet step: whether a staged coordinate lies on the far side of the box from the
+// centre of the cell its atom was binned into (it crossed a face since the cells were
+// built; an atom that has not moves less than half a box from its cell).
+__device__ __forceinline__ bool crossed_face(const float4 &p, const float *centre, const float *half_L)
+{
+    return fabsf(p.x - centre[0]) > half_L[0] || fabsf(p.y - centre[1]) > half_L[1] ||
+           fabsf(p.z - centre[2]) > half_L[2];
+}
+
 // One cell pair: cell cx of the launch (of gx) with stencil entry cy.
-template <int MODE, int STATS, bool BATCHED, bool MI>
+template <int MODE, int STATS, bool BATCHED, bool MI, bool GATHER = false>
 __device__ __forceinline__ void cluster_item(CluSmem<MODE> &sm, float2 *s_ab, const CluArgs &a,
                                              const BatchArgs &bt,
                                              unsigned long long *sys_pair_count, int cx, int cy,
@@ -509,7 +563,7 @@ __device__ __forceinline__ void cluster_item(CluSmem<MODE> &sm, float2 *s_ab, co
         k.rc2m = d.rc2m;
     } else {
         valid = cell_pair(a.box, cx, cy, g);
-        if (MI) {
+        if (MI || GATHER) {
 #pragma unroll
             for (int e = 0; e < 3; ++e) {
                 k.L[e] = (float)a.box.L[e];
@@ -541,7 +595,23 @@ __device__ __forceinline__ void cluster_item(CluSmem<MODE> &sm, float2 *s_ab, co
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         k.lo[d] = g.lo[d];
+        k.hs[d] = g.hs[d];
+        k.ns[d] = g.ns[d];
         shift |= g.lo[d] != 0.0f;
+    }
+    // Verlet step: centres of the two cells and half the box, for the face-crossing test
+    float hcen[3] = {0.f, 0.f, 0.f}, ncen[3] = {0.f, 0.f, 0.f}, half_L[3] = {0.f, 0.f, 0.f};
+    if (GATHER && !MI) {
+        const int nx = a.box.dims[0], ny = a.box.dims[1];
+        const int hc[3] = {g.home % nx, (g.home / nx) % ny, g.home / (nx * ny)};
+        const int nc[3] = {g.nbr % nx, (g.nbr / nx) % ny, g.nbr / (nx * ny)};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const float edge = (float)(a.box.L[d] / a.box.dims[d]);
+            hcen[d] = ((float)hc[d] + 0.5f) * edge;
+            ncen[d] = ((float)nc[d] + 0.5f) * edge;
+            half_L[d] = 0.5f * a.box.Lhi[d];
+        }
     }
     for (int t = threadIdx.x; t < k.T * k.T; t += kCT) {
         const float2 ab = AB[t];
@@ -553,20 +623,34 @@ __device__ __forceinline__ void cluster_item(CluSmem<MODE> &sm, float2 *s_ab, co
         k.hbase = h_begin + h0;
         const int nic = (mh + kCS - 1) / kCS;
         __syncthreads();
-        for (int t = threadIdx.x; t < nic * kCS; t += kCT) {
-            float4 p;
-            int ty = 0;
-            if (t < mh) {
-                p = a.pq[h_begin + h0 + t];
-                p.x -= g.hs[0];
-                p.y -= g.hs[1];
-                p.z -= g.hs[2];
-                ty = clamp_type(a.ty[h_begin + h0 + t], k.T, a.status);
-            } else {
-                p = make_float4(kFar, kFar, kFar, 0.f);
+        // (every thread makes the same number of passes, so that the GATHER form's ballot
+        // sees whole warps)
+        for (int t0 = 0; t0 < (GATHER ? kCTile : nic * kCS); t0 += kCT) {
+            const int t = t0 + threadIdx.x;
+            bool wr = false;
+            if (t < nic * kCS) {
+                float4 p;
+                int ty = 0;
+                if (t < mh) {
+                    const int slot = h_begin + h0 + t;
+                    p = GATHER ? wrap_pos_f(a.gpq[a.perm[slot]], a.box) : a.pq[slot];
+                    wr = GATHER && !MI && crossed_face(p, hcen, half_L);
+                    if (!wr) {  // a wrapped atom is staged as it is
+                        p.x -= g.hs[0];
+                        p.y -= g.hs[1];
+                        p.z -= g.hs[2];
+                    }
+                    ty = clamp_type(a.ty[slot], k.T, a.status);
+                } else {
+                    p = make_float4(kFar, kFar, kFar, 0.f);
+                }
+                sm.hp[t] = p;
+                sm.ht[t] = (unsigned char)ty;
             }
-            sm.hp[t] = p;
-            sm.ht[t] = (unsigned char)ty;
+            if (GATHER) {
+                const unsigned bits = __ballot_sync(0xffffffffu, wr);
+                if ((threadIdx.x & 31) == 0) sm.hwb[t >> 5] = bits;
+            }
         }
         __syncthreads();
         cluster_boxes(sm.hp, mh, sm.ib);
@@ -575,25 +659,38 @@ __device__ __forceinline__ void cluster_item(CluSmem<MODE> &sm, float2 *s_ab, co
             const int njc = (mn + kCS - 1) / kCS;
             const bool diag = g.self && n0 == h0;
             __syncthreads();
-            for (int t = threadIdx.x; t < njc * kCS; t += kCT) {
-                float4 p;
-                int ty = 0;
-                if (t >= mn) {
-                    p = make_float4(-kFar, -kFar, -kFar, 0.f);
-                } else if (diag) {
-                    p = sm.hp[t];  // the home tile holds the same atoms
-                    ty = sm.ht[t];
-                } else {
-                    p = a.pq[n_begin + n0 + t];
-                    p.x -= g.ns[0];
-                    p.y -= g.ns[1];
-                    p.z -= g.ns[2];
-                    ty = clamp_type(a.ty[n_begin + n0 + t], k.T, a.status);
-                }
-                sm.np[t] = p;
-                sm.nt[t] = (unsigned char)ty;
+            for (int t0 = 0; t0 < (GATHER ? kCTile : njc * kCS); t0 += kCT) {
+                const int t = t0 + threadIdx.x;
+                bool wr = false;
+                if (t < njc * kCS) {
+                    float4 p;
+                    int ty = 0;
+                    if (t >= mn) {
+                        p = make_float4(-kFar, -kFar, -kFar, 0.f);
+                    } else if (diag) {
+                        p = sm.hp[t];  // the home tile holds the same atoms
+                        ty = sm.ht[t];
+                        wr = GATHER && wrapped_atom(sm.hwb, t);
+                    } else {
+                        const int slot = n_begin + n0 + t;
+                        p = GATHER ? wrap_pos_f(a.gpq[a.perm[slot]], a.box) : a.pq[slot];
+                        wr = GATHER && !MI && crossed_face(p, ncen, half_L);
+                        if (!wr) {
+                            p.x -= g.ns[0];
+                            p.y -= g.ns[1];
+                            p.z -= g.ns[2];
+                        }
+                        ty = clamp_type(a.ty[slot], k.T, a.status);
+                    }
+                    sm.np[t] = p;
+                    sm.nt[t] = (unsigned char)ty;
 #pragma unroll
-                for (int w = 0; w < CluSmem<MODE>::NW; ++w) sm.react(w, 0, t) = sm.react(w, 1, t) = sm.react(w, 2, t) = Acc(0);
+                    for (int w = 0; w < CluSmem<MODE>::NW; ++w) sm.react(w, 0, t) = sm.react(w, 1, t) = sm.react(w, 2, t) = Acc(0);
+                }
+                if (GATHER) {
+                    const unsigned bits = __ballot_sync(0xffffffffu, wr);
+                    if ((threadIdx.x & 31) == 0) sm.jwb[t >> 5] = bits;
+                }
             }
             __syncthreads();
             cluster_boxes(sm.np, mn, sm.jb);
@@ -604,11 +701,11 @@ __device__ __forceinline__ void cluster_item(CluSmem<MODE> &sm, float2 *s_ab, co
             // so that every warp-private partial sum is formed in the same order each run
             for (int ic = warp; ic < nic;) {
                 if (diag)
-                    cluster_row<MODE, STATS, true, false, MI>(sm, s_ab, k, ic, njc, mh, warp, lane, e_lj, e_c, vir, cnt);
+                    cluster_row<MODE, STATS, true, false, MI, GATHER>(sm, s_ab, k, ic, njc, mh, warp, lane, e_lj, e_c, vir, cnt);
                 else if (!MI && shift)
-                    cluster_row<MODE, STATS, false, true, false>(sm, s_ab, k, ic, njc, mh, warp, lane, e_lj, e_c, vir, cnt);
+                    cluster_row<MODE, STATS, false, true, false, GATHER>(sm, s_ab, k, ic, njc, mh, warp, lane, e_lj, e_c, vir, cnt);
                 else
-                    cluster_row<MODE, STATS, false, false, MI>(sm, s_ab, k, ic, njc, mh, warp, lane, e_lj, e_c, vir, cnt);
+                    cluster_row<MODE, STATS, false, false, MI, GATHER>(sm, s_ab, k, ic, njc, mh, warp, lane, e_lj, e_c, vir, cnt);
                 if (MODE == MD_ACCUM_FIXED_TILE) {
                     ic += kCW;
                 } else {
@@ -670,7 +767,7 @@ constexpr int clu_min_blocks()
          : (MODE != MD_ACCUM_FIXED64 && STATS == kStatsNone) ? 9 : 8;
 }
 
-template <int MODE, int STATS, bool BATCHED, bool MI, bool PERSIST>
+template <int MODE, int STATS, bool BATCHED, bool MI, bool PERSIST, bool GATHER = false>
 __global__ void __launch_bounds__(kCT, (clu_min_blocks<MODE, STATS, PERSIST>()))
 k_cluster(CluArgs a, BatchArgs bt, unsigned long long *sys_pair_count, int *work, int ncells,
           int per_cell)
@@ -681,8 +778,8 @@ k_cluster(CluArgs a, BatchArgs bt, unsigned long long *sys_pair_count, int *work
     pdl_wait();
     pdl_trigger();
     if (!PERSIST) {
-        cluster_item<MODE, STATS, BATCHED, MI>(sm, s_ab, a, bt, sys_pair_count, blockIdx.x, blockIdx.y,
-                                               gridDim.x);
+        cluster_item<MODE, STATS, BATCHED, MI, GATHER>(sm, s_ab, a, bt, sys_pair_count, blockIdx.x,
+                                                       blockIdx.y, gridDim.x);
         return;
     }
     __shared__ int s_item;
@@ -743,14 +840,15 @@ k_finalize_clu(const void *__restrict__ accum, const int32_t *__restrict__ corde
 
 // grid: cells x stencil entries.  PERSIST: the same items from about one wave of CTAs
 // (blocks per SM at this launch's shared memory x SMs), taking items from `work`.
-template <int MODE, int STATS, bool BATCHED = false, bool MI = false, bool PERSIST = false>
+template <int MODE, int STATS, bool BATCHED = false, bool MI = false, bool PERSIST = false,
+          bool GATHER = false>
 cudaError_t launch_cluster_t(const CluArgs &c, dim3 grid, cudaStream_t stream,
                              const BatchArgs &b = BatchArgs{},
                              unsigned long long *sys_pair_count = nullptr, int *work = nullptr)
 {
     const size_t dyn = sizeof(float2) * (size_t)c.ntypes * (size_t)c.ntypes;
     static const cudaError_t attr = cudaFuncSetAttribute(
-        k_cluster<MODE, STATS, BATCHED, MI, PERSIST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        k_cluster<MODE, STATS, BATCHED, MI, PERSIST, GATHER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
         (int)(sizeof(float2) * kMaxTypes * kMaxTypes));
     (void)attr;
     dim3 g = grid;
@@ -759,22 +857,34 @@ cudaError_t launch_cluster_t(const CluArgs &c, dim3 grid, cudaStream_t stream,
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cluster<MODE, STATS, BATCHED, MI, PERSIST>,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cluster<MODE, STATS, BATCHED, MI, PERSIST, GATHER>,
                                                       kCT, dyn);
         const long long wave = (long long)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
         const long long items = (long long)grid.x * grid.y;
         g = dim3((unsigned)(items < wave ? items : wave), 1);
     }
-    return launch_pdl(k_cluster<MODE, STATS, BATCHED, MI, PERSIST>, g, dim3(kCT), dyn, stream, c, b,
+    return launch_pdl(k_cluster<MODE, STATS, BATCHED, MI, PERSIST, GATHER>, g, dim3(kCT), dyn, stream, c, b,
                       sys_pair_count, work, (int)grid.x, (int)grid.y);
 }
 
-template <int MODE, bool MI>
+template <int MODE, bool MI, bool GATHER = false>
 cudaError_t launch_cluster_stats(int stats, const CluArgs &c, dim3 grid, cudaStream_t stream)
 {
-    if (stats == kStatsEnergy) return launch_cluster_t<MODE, kStatsEnergy, false, MI>(c, grid, stream);
-    if (stats == kStatsCount) return launch_cluster_t<MODE, kStatsCount, false, MI>(c, grid, stream);
-    return launch_cluster_t<MODE, kStatsNone, false, MI>(c, grid, stream);
+    if (stats == kStatsEnergy) return launch_cluster_t<MODE, kStatsEnergy, false, MI, false, GATHER>(c, grid, stream);
+    // the Verlet step asks for forces, or forces and energies
+    if (stats == kStatsCount && !GATHER) return launch_cluster_t<MODE, kStatsCount, false, MI>(c, grid, stream);
+    return launch_cluster_t<MODE, kStatsNone, false, MI, false, GATHER>(c, grid, stream);
+}
+
+template <int MODE>
+cudaError_t launch_cluster_mode(bool mi, bool gather, int stats, const CluArgs &c, dim3 grid,
+                                cudaStream_t stream)
+{
+    if (gather)
+        return mi ? launch_cluster_stats<MODE, true, true>(stats, c, grid, stream)
+                  : launch_cluster_stats<MODE, false, true>(stats, c, grid, stream);
+    return mi ? launch_cluster_stats<MODE, true>(stats, c, grid, stream)
+              : launch_cluster_stats<MODE, false>(stats, c, grid, stream);
 }
 
 }  // namespace
@@ -810,18 +920,18 @@ cudaError_t launch_cluster(const ForceArgs &a, const WsLayout &ws, char *wsp, Pa
     c.n = a.n;
     c.partials = partials;
     c.status = a.status;
+    c.gpq = a.gather_pq;
+    c.perm = a.perm;
+    const bool gather = a.gather_pq != nullptr;
+    if (gather && !a.presorted) return cudaErrorInvalidValue;
     dim3 grid(a.box.ncell, per_cell);
     const int stats = a.energy_virial_out ? kStatsEnergy : (a.pair_count_out ? kStatsCount : kStatsNone);
-    if (a.mode == MD_ACCUM_FIXED64) {
-        e = mi ? launch_cluster_stats<MD_ACCUM_FIXED64, true>(stats, c, grid, stream)
-               : launch_cluster_stats<MD_ACCUM_FIXED64, false>(stats, c, grid, stream);
-    } else if (a.mode == MD_ACCUM_FIXED_TILE) {
-        e = mi ? launch_cluster_stats<MD_ACCUM_FIXED_TILE, true>(stats, c, grid, stream)
-               : launch_cluster_stats<MD_ACCUM_FIXED_TILE, false>(stats, c, grid, stream);
-    } else {
-        e = mi ? launch_cluster_stats<MD_ACCUM_F32, true>(stats, c, grid, stream)
-               : launch_cluster_stats<MD_ACCUM_F32, false>(stats, c, grid, stream);
-    }
+    if (a.mode == MD_ACCUM_FIXED64)
+        e = launch_cluster_mode<MD_ACCUM_FIXED64>(mi, gather, stats, c, grid, stream);
+    else if (a.mode == MD_ACCUM_FIXED_TILE)
+        e = launch_cluster_mode<MD_ACCUM_FIXED_TILE>(mi, gather, stats, c, grid, stream);
+    else
+        e = launch_cluster_mode<MD_ACCUM_F32>(mi, gather, stats, c, grid, stream);
     *nblocks_out = a.box.ncell * per_cell;
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -74,6 +74,8 @@ struct WsLayout {
     size_t clu_pos_q, clu_type, clu_order;  // cluster-pair kernel: per-cell reordered copies
     size_t work;        // int[2] item counters of persistent force launches
     size_t bins;        // int32 [ncell][bin_cap] members of each cell by arrival (MD step)
+    size_t v_ref;       // float4 [n]  positions at the last cell rebuild (Verlet step only)
+    size_t v_flags;     // VerletFlags (Verlet step only)
     size_t total;
     int nslots;
     int bin_cap;        // 0: no bins (the step scatters through perm_tmp)
@@ -82,7 +84,13 @@ struct WsLayout {
 // Members per cell that the MD step's bins hold: twice the mean occupancy plus 64,
 // rounded up to 32.  A cell with more members is gathered by a scan of the cell ids.
 int bin_capacity(int n, int ncell);
-WsLayout ws_layout(int n, int ncell, bool bins = true);
+WsLayout ws_layout(int n, int ncell, bool bins = true, bool verlet = false);
+
+// Device state of the Verlet step (md_step_verlet), in its workspace.
+struct VerletFlags {
+    int rebuild;             // the cells of this step are rebuilt (1) or kept (0)
+    unsigned maxdisp2;       // bits of the largest squared move since the rebuild (a float)
+};
 
 // Layout of the batch workspace (byte offsets), derived on the host from the systems.
 struct BatchLayout {
@@ -427,6 +435,9 @@ struct ForceArgs {
     // the build pass of the MD step already zeroed the cluster-order accumulators (and
     // the persistent launches' item counters)
     int accum_zeroed = 0;
+    // Verlet step: the cells (cell_start, perm, type_sorted) are those of the last rebuild
+    // and the current positions come from this input-order float copy through perm
+    const float4 *gather_pq = nullptr;
     // optional half kick v += dt/2 a(F) applied as the forces are written (MD step)
     double *kick_vel = nullptr;
     const float *kick_inv_mass = nullptr;
@@ -469,6 +480,20 @@ cudaError_t launch_forces_batched(const ForceArgs &a, const BatchArgs &b,
 
 cudaError_t launch_kick(double *vel, const void *forces, int mode, const float *inv_mass, int n,
                         double half_dt, cudaStream_t stream);
+
+// Verlet step passes (md_verlet.cu and md_cells.cu).
+cudaError_t launch_verlet_drift(double *pos, double *vel, const void *forces, int mode,
+                                const float *inv_mass, const float *q, int n, const BoxF &box,
+                                double dt, double half_dt, bool kick, float4 *pos_q,
+                                const float4 *x_ref, void *accum, VerletFlags *flags,
+                                uint32_t *status, cudaStream_t stream);
+cudaError_t launch_verlet_decide(VerletFlags *flags, float threshold2, bool force,
+                                 unsigned long long *rebuilds, cudaStream_t stream);
+cudaError_t launch_verlet_rebuild(const float4 *pos_q, const int32_t *type, int n, const BoxF &box,
+                                  int32_t *cell_start, int32_t *perm, float4 *pos_q_sorted,
+                                  int32_t *type_sorted, float4 *x_ref, const int *run_flag,
+                                  const WsLayout &ws, char *wsp, uint32_t *status,
+                                  cudaStream_t stream);
 cudaError_t launch_energy_log_row(const double *vel, const float *inv_mass, int n,
                                   const double *energy_virial, double *row, const WsLayout &ws,
                                   char *wsp, cudaStream_t stream);

@@ -125,3 +125,21 @@ def test_fixed_tile_mode_only_on_the_cluster_kernel(lib):
         assert lib.md_batch_step_tuned(1, ctypes.byref(desc), None, None, None, 0, None, None,
                                        None, api.ACCUM_FIXED_TILE, 1.0, 1, None, None, 0, None,
                                        ctypes.byref(t), None) == -1
+
+
+def test_verlet_step_validation(lib):
+    from paper_1611_04474_gb300 import api
+
+    box = (ctypes.c_double * 3)(30.0, 30.0, 30.0)
+    assert lib.md_verlet_workspace_bytes(1000, box, 12.0, 1.0) > 0
+    # rc + skin must stay below L/2
+    assert lib.md_verlet_workspace_bytes(1000, box, 12.0, 3.0) == 0
+    assert lib.md_verlet_workspace_bytes(1000, box, 12.0, 0.0) == 0
+    ff = api.md_forcefield(4, 0, 256, 332.0636, 12.0)
+    P = ctypes.c_void_p(16)  # never dereferenced: validation fails first
+    args = lambda mode, skin: (P, P, P, 0, P, P, P, 10, box, ctypes.byref(ff), mode, 1.0, 1, skin,
+                               None, None, None, 0, None, None)
+    assert lib.md_step_verlet(*args(api.ACCUM_F32, 0.0)) == -1        # skin <= 0
+    assert lib.md_step_verlet(*args(api.ACCUM_F32, 3.5)) == -2        # rc + skin >= L/2
+    assert lib.md_step_verlet(*args(api.ACCUM_F64, 1.0)) == -1        # the FP64 mode
+    assert lib.md_step_verlet(*args(api.ACCUM_F32, 1.0)) == -3        # no workspace
