@@ -99,6 +99,8 @@ def parse():
     ap.add_argument("--dt", type=float, default=1.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batch, serving and Verlet-skin measurements")
     return ap.parse_args()
 
 
@@ -263,6 +265,58 @@ def measure_peak(dev_index: int):
     clk = clocks.stop()
     out["sm_mhz"] = clk.get("sm_mhz")
     out["reasons"] = clk.get("reasons")
+    return out
+
+
+def measure_extras(eng, args):
+    """The project's other operating points on this GPU, each with its own timing: the
+    256-system batch (FIXED_TILE, CUDA-graph replay, against each system alone with
+    md_step), the serving loop on two Poisson windows (against one job at a time, every
+    job's stand-alone time measured), and the MD step with a Verlet skin."""
+    import torch
+
+    from paper_1611_04474_gb300 import api
+    from paper_1611_04474_gb300 import run_batch, run_serve
+    from paper_1611_04474_gb300 import workloads as W
+
+    out = {}
+    t0 = time.perf_counter()
+    systems = W.batch_of_systems()
+    b = run_batch.measure_batch(systems, 50, api.ACCUM_FIXED_TILE)
+    b64 = run_batch.measure_batch(systems, 50, api.ACCUM_FIXED64, graph=False, alone=False)
+    b.update({"mode": "fixed_tile", "workload": "256 systems, N log-uniform 500-20,000, 50 steps",
+              "fixed64_batch_loop_ms": b64["batch_loop_ms"],
+              "fixed64_pairs_per_s_batch_loop": b64["pairs_per_s_batch_loop"],
+              "seconds": time.perf_counter() - t0})
+    out["batch"] = b
+    t0 = time.perf_counter()
+    serve = {}
+    for rate, n in ((200.0, 150), (15.0, 80)):
+        r = run_serve.serve_window(rate, n, api.ACCUM_FIXED_TILE)
+        keep = ("jobs", "latency_p50_s", "latency_p99_s", "pairs_per_s", "offered_jobs_per_s",
+                "achieved_jobs_per_s", "rebuilds", "ticks", "alone")
+        serve[f"rate_{int(rate)}"] = {k: r[k] for k in keep}
+    serve["mode"] = "fixed_tile"
+    serve["workload"] = "Poisson arrivals, N log-uniform 1,000-150,000, 10-500 steps"
+    serve["seconds"] = time.perf_counter() - t0
+    out["serve"] = serve
+    t0 = time.perf_counter()
+    verlet = {}
+    s = eng.system
+    for skin in (0.5, 1.0):
+        v = api.Engine(s, mode=eng.mode)
+        v.step(3, dt_fs=args.dt)
+        v.rebuilds = torch.zeros(1, dtype=torch.int64, device=v.pos.device)
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        v.step_verlet(100, dt_fs=args.dt, skin=skin)
+        z.record()
+        torch.cuda.synchronize()
+        verlet[f"skin_{skin}"] = {"ms_per_step": a.elapsed_time(z) / 100,
+                                  "cell_builds_per_100_steps": int(v.rebuilds.item())}
+    verlet["seconds"] = time.perf_counter() - t0
+    out["verlet"] = verlet
     return out
 
 
@@ -543,6 +597,8 @@ def run_ours(args):
         "clocks": clk,
         "status": status,
     }
+    if rank == 0 and not args.no_extras:
+        line.update(measure_extras(eng, args))
     if rank == 0 and not args.no_cpu_baseline:
         from paper_1611_04474_gb300 import workloads as W
 

@@ -72,6 +72,14 @@ def _store(path, key, entry):
         os.replace(tmp, path)
 
 
+def shapes_for(mode) -> list:
+    """The kernel shapes a mode can run: MD_ACCUM_FIXED_TILE exists in the cluster kernel
+    only (shapes 0 and 5)."""
+    if mode == api.ACCUM_FIXED_TILE:
+        return [0, 5]
+    return list(range(api.BATCH_SHAPES))
+
+
 def _time_shape(batch, tuning, n_steps, reps):
     """Mean ms of ``batch.step(n_steps)`` with ``tuning`` (state restored by the caller)."""
     batch.tuning = tuning
@@ -99,12 +107,12 @@ def measure(batch, n_steps=5, reps=3):
             if not present:
                 continue
             t = []
-            for shape in range(api.BATCH_SHAPES):
+            for shape in shapes_for(batch.mode):
                 trial = list(best)
                 trial[idx] = shape
-                t.append(_time_shape(batch, tuple(trial), n_steps, reps))
-            best[idx] = int(np.argmin(t))
-            times[name] = t
+                t.append((_time_shape(batch, tuple(trial), n_steps, reps), shape))
+            best[idx] = min(t)[1]
+            times[name] = {str(sh): ms for ms, sh in t}
     finally:
         for k, v in saved.items():
             getattr(batch, k).copy_(v)
@@ -119,7 +127,7 @@ def tune(batch, cache_path: str | None = DEFAULT_CACHE, n_steps=5, reps=3, retun
     key = cache_key(batch)
     if cache_path and not retune:
         hit = _load(cache_path).get(key)
-        if hit and all(0 <= int(v) < api.BATCH_SHAPES for v in hit.get("tuning", [])) \
+        if hit and all(int(v) in shapes_for(batch.mode) for v in hit.get("tuning", [])) \
                 and len(hit.get("tuning", [])) == 2:
             batch.tuning = tuple(int(v) for v in hit["tuning"])
             return dict(hit, measured=False, key=key)

@@ -1,55 +1,58 @@
-"""Serving measurement: a Poisson stream of MD jobs through the continuous-batching
-server, against serving the same arrivals one job at a time with the plain md_step
-path (stand-alone job times measured on a sample of the jobs and fitted as a linear
-function of each job's pair count).
+"""Serving measurement: Poisson streams of MD jobs through the continuous-batching server,
+against serving the same arrivals one job at a time with the plain md_step path, whose
+stand-alone device time is measured for every job of the window.
 
-    python -m paper_1611_04474_gb300.run_serve --jobs 400 --rate 200
+    python -m paper_1611_04474_gb300.run_serve --rates 15,50,200 --jobs 300,600,2000
 """
 from __future__ import annotations
 
 import argparse
 import json
 
-import numpy as np
-
 from . import api
 from . import serve
 from . import workloads as W
 
+MODES = {"f32": api.ACCUM_F32, "fixed64": api.ACCUM_FIXED64, "fixed_tile": api.ACCUM_FIXED_TILE}
+
+
+def serve_window(rate: float, n_jobs: int, mode: int, seed: int = 5, tick: int = 10,
+                 budget_gb: float = 16.0, n_range=(1000, 150000), steps_range=(10, 500)):
+    """One window: serve, then time every job alone; returns the result dict."""
+    specs = W.serving_jobs(n_jobs=n_jobs, rate_per_s=rate, seed=seed, n_range=n_range,
+                           steps_range=steps_range)
+    jobs = [serve.Job(k, mk, st, arr, n) for k, (mk, st, arr, n) in enumerate(specs)]
+    srv = serve.Server(mode=mode, budget_bytes=int(budget_gb * (1 << 30)), tick_steps=tick)
+    res = srv.run(jobs)
+    res.update({"rate": rate, "tick_steps": tick, "ticks": srv.ticks, "step_calls": srv.calls,
+                "rebuilds": srv.rebuilds, "max_footprint_gb": srv.max_footprint / (1 << 30),
+                "loop_seconds": {k: round(v, 3) for k, v in srv.seconds.items()}})
+    # one job at a time: each job's md_step run alone, on the system it was served with
+    alone = [serve.time_alone(j, mode, system=j.system) for j in jobs]
+    res["alone"] = serve.fifo_alone(jobs, alone)
+    res["alone"]["device_seconds"] = float(sum(alone))
+    res["alone"]["measured_jobs"] = len(alone)
+    return res
+
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--jobs", type=int, default=400)
-    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--rates", default="200", help="comma-separated Poisson rates (jobs/s)")
+    ap.add_argument("--jobs", default="400", help="comma-separated window sizes, one per rate")
     ap.add_argument("--seed", type=int, default=5)
     ap.add_argument("--tick", type=int, default=10)
     ap.add_argument("--budget-gb", type=float, default=16.0)
-    ap.add_argument("--alone-sample", type=int, default=30)
-    ap.add_argument("--mode", default="fixed64", choices=["f32", "fixed64"])
+    ap.add_argument("--mode", default="fixed_tile", choices=list(MODES))
     args = ap.parse_args(argv)
-    mode = api.ACCUM_F32 if args.mode == "f32" else api.ACCUM_FIXED64
-    specs = W.serving_jobs(n_jobs=args.jobs, rate_per_s=args.rate, seed=args.seed)
-    jobs = [serve.Job(k, mk, st, arr, n) for k, (mk, st, arr, n) in enumerate(specs)]
-    srv = serve.Server(mode=mode, budget_bytes=int(args.budget_gb * (1 << 30)), tick_steps=args.tick)
-    res = srv.run(jobs)
-    res.update({"mode": args.mode, "rate": args.rate, "tick_steps": args.tick,
-                "ticks": srv.ticks, "rebuilds": srv.rebuilds,
-                "max_footprint_gb": srv.max_footprint / (1 << 30),
-                "loop_seconds": {k: round(v, 3) for k, v in srv.seconds.items()}})
-    # stand-alone times on a sample of jobs, fitted as a + b * pairs
-    rng = np.random.default_rng(0)
-    sample = rng.choice(len(jobs), size=min(args.alone_sample, len(jobs)), replace=False)
-    xs, ys = [], []
-    for k in sample:
-        ys.append(serve.time_alone(jobs[k], mode))
-        xs.append(jobs[k].pairs)
-    A = np.vstack([np.ones(len(xs)), np.asarray(xs, dtype=np.float64)]).T
-    coef = np.linalg.lstsq(A, np.asarray(ys), rcond=None)[0]
-    alone = [max(coef[0] + coef[1] * j.pairs, 0.0) for j in jobs]
-    res["alone"] = serve.fifo_alone(jobs, alone)
-    res["alone_fit"] = {"seconds_fixed": float(coef[0]), "seconds_per_pair": float(coef[1]),
-                        "sample": len(sample)}
-    print(json.dumps(res))
+    rates = [float(x) for x in args.rates.split(",")]
+    sizes = [int(x) for x in args.jobs.split(",")]
+    if len(sizes) == 1:
+        sizes = sizes * len(rates)
+    for rate, n in zip(rates, sizes):
+        res = serve_window(rate, n, MODES[args.mode], seed=args.seed, tick=args.tick,
+                           budget_gb=args.budget_gb)
+        res["mode"] = args.mode
+        print(json.dumps(res), flush=True)
 
 
 if __name__ == "__main__":

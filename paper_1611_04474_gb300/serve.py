@@ -2,13 +2,23 @@
 
 Jobs (a periodic system and a number of velocity-Verlet steps) arrive over time.  The
 server keeps every admitted job's state on the device and advances all active jobs
-together: each tick is one md_batch_step over the current set, so the work of jobs
-that arrived at different times overlaps on the GPU.  Between ticks finished jobs
-leave and queued jobs join while their device-memory footprint fits the budget
-(admission in arrival order).  When the set changes, the active jobs' state is written
-back from the batch arena and a new arena is built, and their forces are recomputed
-at the current positions; in MD_ACCUM_FIXED64 that recomputation gives the same bits,
-so a job's result does not depend on the company it ran in.
+together in one arena (an md_batch_step over their concatenation), so the work of jobs
+that arrived at different times overlaps on the GPU.
+
+A tick advances the arena by up to `tick_steps` steps, split into md_batch_step calls
+at the steps where jobs reach their last step: such a job's state is copied out right
+after its last step (on the stream, no host wait) and it stays in the arena, advanced
+but no longer counted, until the arena is next rebuilt.  The arena is rebuilt between
+ticks when the jobs waiting to join carry enough atoms or have waited `max_wait_s`, or
+when finished jobs fill half of it; rebuilding copies the live jobs' state from the old
+arena (device to device) and recomputes their forces at the current positions.  In
+the deterministic modes (MD_ACCUM_FIXED_TILE, the default, and MD_ACCUM_FIXED64) that
+recomputation gives the same bits, and a system's result never depends on the other
+systems of its batch, so a job's result is the same as running it alone.
+
+The host enqueues ticks ahead of the GPU (at most `depth` in flight) and learns of
+finished jobs from CUDA events; pair counts accumulate on the device and are read once
+at the end.
 
 Reported per run: job latencies (finish - arrival; p50, p99), the aggregate within-
 cutoff pair rate, the achieved against the offered job rate, and the largest
@@ -57,19 +67,33 @@ class Job:
 
 
 class Server:
-    def __init__(self, mode=api.ACCUM_FIXED64, budget_bytes: int = 16 << 30, tick_steps: int = 10,
-                 dt_fs: float = 1.0, device="cuda", lookahead: int = 32):
+    def __init__(self, mode=api.ACCUM_FIXED_TILE, budget_bytes: int = 16 << 30,
+                 tick_steps: int = 10, dt_fs: float = 1.0, device="cuda", lookahead: int = 32,
+                 depth: int = 2, max_wait_s: float = 0.002, join_fraction: float = 0.2,
+                 active_atoms: int = 400_000, tick_ms: float = 4.0):
         self.mode = mode
         self.budget = int(budget_bytes)
         self.tick = int(tick_steps)
         self.dt = float(dt_fs)
         self.device = torch.device(device)
         self.lookahead = int(lookahead)
+        self.depth = int(depth)
+        self.max_wait = float(max_wait_s)
+        self.join_fraction = float(join_fraction)
+        # compute admission: jobs join the arena while its live atoms stay below this
+        # (enough to fill the GPU; beyond it more company only slows every job down), so
+        # that under overload jobs wait in arrival order instead of all sharing the GPU
+        self.active_atoms = int(active_atoms)
+        # a tick runs about tick_ms of GPU time (at least tick_steps steps), so that the
+        # host's work per tick stays small beside the GPU's
+        self.tick_ms = float(tick_ms)
         self.max_footprint = 0
         self.ticks = 0
+        self.calls = 0
         self.rebuilds = 0
-        # wall seconds of the serving loop by phase
-        self.seconds = {"upload": 0.0, "rebuild": 0.0, "ticks": 0.0, "write_back": 0.0}
+        self.ms_per_step = None  # of the current arena, from its last completed tick
+        # wall seconds of the serving loop by phase (host time; the GPU runs ahead)
+        self.seconds = {"upload": 0.0, "rebuild": 0.0, "enqueue": 0.0, "wait": 0.0}
 
     # ---------------------------------------------------------------- job state
     def _receive(self, ordered, admitted_count, stop):
@@ -92,35 +116,27 @@ class Server:
         j.ff = api.ForceField.from_system(s, self.device)
         d = self.device
         j.state = {
-            "pos": torch.as_tensor(s.pos.astype(np.float64)).to(d),
-            "vel": torch.as_tensor(s.vel).to(d),
+            "pos": torch.as_tensor(s.pos.astype(np.float64)).to(d, non_blocking=True),
+            "vel": torch.as_tensor(s.vel).to(d, non_blocking=True),
             "forces": torch.zeros((s.n, 3), dtype=api.FORCE_DTYPE[self.mode], device=d),
-            "q": torch.as_tensor(s.q).to(d),
-            "types": torch.as_tensor(s.type).to(d),
-            "inv_mass": torch.as_tensor(s.inv_mass).to(d),
+            "q": torch.as_tensor(s.q).to(d, non_blocking=True),
+            "types": torch.as_tensor(s.type).to(d, non_blocking=True),
+            "inv_mass": torch.as_tensor(s.inv_mass).to(d, non_blocking=True),
         }
         j.remaining = j.n_steps
 
-    def _arena(self, active, prev=None, prev_active=()):
-        """A batch over `active`: jobs that were in the previous arena bring their
+    def _arena(self, members, prev=None, prev_members=()):
+        """A batch over `members`: jobs that were in the previous arena bring their
         current state straight from it (device to device), new jobs from their own."""
-        where = {id(j): k for k, j in enumerate(prev_active)}
+        where = {id(j): k for k, j in enumerate(prev_members)}
         keys = ("pos", "vel", "forces", "q", "types", "inv_mass")
 
         def src(j, key):
             k = where.get(id(j))
             return j.state[key] if k is None else getattr(prev, key)[prev.system_slice(k)]
-        state = {key: torch.cat([src(j, key) for j in active]).contiguous() for key in keys}
-        return api.Batch([j.system for j in active], mode=self.mode, device=self.device,
-                         state=state, ffs=[j.ff for j in active])
-
-    def _write_back(self, batch, active, jobs):
-        """The current state of `jobs` (a subset of `active`) into their own tensors."""
-        for k, j in enumerate(active):
-            if any(j is x for x in jobs):
-                sl = batch.system_slice(k)
-                for key in ("pos", "vel", "forces"):
-                    j.state[key].copy_(getattr(batch, key)[sl])
+        state = {key: torch.cat([src(j, key) for j in members]).contiguous() for key in keys}
+        return api.Batch([j.system for j in members], mode=self.mode, device=self.device,
+                         state=state, ffs=[j.ff for j in members])
 
     # ---------------------------------------------------------------- main loop
     def run(self, jobs, realtime: bool = True):
@@ -141,19 +157,53 @@ class Server:
 
     def _serve(self, pending, admitted_count, realtime):
         jobs = list(pending)
-        queue = collections.deque()
-        active = []
-        footprint = 0
+        index = {id(j): k for k, j in enumerate(jobs)}
+        dev = self.device
+        pairs_dev = torch.zeros(len(jobs), dtype=torch.int64, device=dev)
+        status_dev = torch.zeros(1, dtype=torch.int32, device=dev)
+        queue = collections.deque()   # arrived, not admitted
+        waiting = []                  # admitted, not yet in the arena
+        members = []                  # the arena's jobs, in its order (live and finished)
         batch = None
-        in_batch = []  # the jobs of `batch`, in its order
-        changed = True
+        footprint = 0                 # admitted jobs' memory, finished ones until a rebuild
+        inflight = collections.deque()  # (event, jobs whose last step precedes it, timing)
         t0 = time.perf_counter()
         now = lambda: time.perf_counter() - t0  # noqa: E731
-        while pending or queue or active:
+
+        def retire(block):
+            # finish times of the jobs whose last step the GPU has completed
+            while inflight:
+                ev, done, timing = inflight[0]
+                if not ev.query():
+                    if not block:
+                        return
+                    t1 = time.perf_counter()
+                    ev.synchronize()
+                    self.seconds["wait"] += time.perf_counter() - t1
+                t = now()
+                for j in done:
+                    j.finished = t
+                if timing is not None and timing[2] is batch:  # (start event, steps, arena)
+                    self.ms_per_step = timing[0].elapsed_time(ev) / max(timing[1], 1)
+                inflight.popleft()
+                block = False
+
+        def counts_of(b, mem, which):
+            # add the arena's counts of `which` (members) to the jobs' totals, on the stream
+            ks = [k for k, j in enumerate(mem) if any(j is x for x in which)]
+            if ks:
+                sel = torch.tensor(ks, dtype=torch.int64, device=dev)
+                dst = torch.tensor([index[id(mem[k])] for k in ks], dtype=torch.int64, device=dev)
+                pairs_dev.index_add_(0, dst, b.pair_count.index_select(0, sel))
+
+        while pending or queue or waiting or any(j.remaining for j in members):
+            retire(False)
             t = now() if realtime else math.inf
             while pending and pending[0].arrival <= t:
                 queue.append(pending.popleft())
-            while queue and footprint + job_footprint_bytes(queue[0].n_atoms) <= self.budget:
+            in_flight_atoms = sum(j.n_atoms for j in members if j.remaining > 0) + sum(j.n_atoms for j in waiting)
+            while queue and footprint + job_footprint_bytes(queue[0].n_atoms) <= self.budget and (
+                    in_flight_atoms == 0 or in_flight_atoms + queue[0].n_atoms <= self.active_atoms):
                 j = queue.popleft()
                 t1 = time.perf_counter()
                 self._load(j)
@@ -162,53 +212,95 @@ class Server:
                     admitted_count.n += 1
                     admitted_count.notify_all()
                 j.admitted = now()
-                active.append(j)
+                waiting.append(j)
                 footprint += job_footprint_bytes(j.n_atoms)
-                changed = True
+                in_flight_atoms += j.n_atoms
             self.max_footprint = max(self.max_footprint, footprint)
-            if not active:
-                if queue:
+            live = [j for j in members if j.remaining > 0]
+            live_atoms = sum(j.n_atoms for j in live)
+            done_atoms = sum(j.n_atoms for j in members if j.remaining == 0)
+            wait_atoms = sum(j.n_atoms for j in waiting)
+            if not live and not waiting:
+                if queue and not members:
                     raise RuntimeError(f"job {queue[0].id} alone exceeds the memory budget")
-                if pending:
+                if not members and pending:
+                    retire(True)
                     time.sleep(max(0.0, pending[0].arrival - now()))
-                continue
-            if changed:
+                    continue
+            done_bytes = sum(job_footprint_bytes(j.n_atoms) for j in members if j.remaining == 0)
+            head_fits_after = bool(queue) and footprint - done_bytes + job_footprint_bytes(queue[0].n_atoms) <= self.budget
+            rebuild = bool((not live and (waiting or members)) or (
+                waiting and (wait_atoms >= self.join_fraction * live_atoms
+                             or now() - min(j.admitted for j in waiting) >= self.max_wait)) or (
+                members and done_atoms >= live_atoms) or (done_bytes and head_fits_after))
+            if rebuild:
                 t1 = time.perf_counter()
-                batch = self._arena(active, batch, in_batch)
-                in_batch = list(active)
-                batch.step(0)  # forces of the current positions (first call: not yet valid)
+                if batch is not None:
+                    counts_of(batch, members, live)
+                    status_dev.bitwise_or_(batch.status)
+                freed = sum(job_footprint_bytes(j.n_atoms) for j in members if j.remaining == 0)
+                new_members = live + waiting
+                batch = self._arena(new_members, batch, members) if new_members else None
+                members, waiting = new_members, []
+                footprint -= freed
+                if batch is not None:
+                    batch.step(0)  # forces of the current positions
+                self.ms_per_step = None
                 self.rebuilds += 1
-                changed = False
                 self.seconds["rebuild"] += time.perf_counter() - t1
-            k = min(self.tick, min(j.remaining for j in active))
+                continue
+            if not live:
+                retire(True)
+                if pending:
+                    time.sleep(max(0.0, min(self.max_wait, pending[0].arrival - now())))
+                continue
+            # one tick: md_batch_step calls split where live jobs take their last step
             t1 = time.perf_counter()
-            batch.pair_count.zero_()
-            batch.step(k, dt_fs=self.dt, count_pairs=True)
-            counts = batch.pair_count.cpu().numpy()  # waits for the tick
-            self.seconds["ticks"] += time.perf_counter() - t1
+            left = self.tick
+            if self.ms_per_step:
+                left = max(self.tick, min(500, int(self.tick_ms / self.ms_per_step)))
+            tick_steps = left
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev0.record()
+            while left > 0:
+                live = [j for j in members if j.remaining > 0]
+                if not live:
+                    break
+                k = min(left, min(j.remaining for j in live))
+                batch.step(k, dt_fs=self.dt, count_pairs=True)
+                self.calls += 1
+                left -= k
+                done = []
+                for j in live:
+                    j.remaining -= k
+                    if j.remaining == 0:
+                        done.append(j)
+                if done:
+                    # their final state and counts, right after their last step
+                    for j in done:
+                        sl = batch.system_slice(next(i for i, x in enumerate(members) if x is j))
+                        for key in ("pos", "vel", "forces"):
+                            j.state[key].copy_(getattr(batch, key)[sl])
+                    counts_of(batch, members, done)
+                    ev = torch.cuda.Event()
+                    ev.record()
+                    inflight.append((ev, done, None))
+            ev = torch.cuda.Event(enable_timing=True)
+            ev.record()
+            inflight.append((ev, [], (ev0, tick_steps - left, batch)))
             self.ticks += 1
-            t = now()
-            done = []
-            for idx, j in enumerate(active):
-                j.remaining -= k
-                j.pairs += int(counts[idx])
-                if j.remaining == 0:
-                    done.append(j)
-            if int(batch.status.item()) != 0:
-                raise RuntimeError(f"device status {int(batch.status.item())} during serving")
-            freed = sum(job_footprint_bytes(j.n_atoms) for j in done)
-            head = queue[0] if queue else (pending[0] if pending and realtime and pending[0].arrival <= now() else None)
-            joinable = head is not None and footprint - freed + job_footprint_bytes(head.n_atoms) <= self.budget
-            if done or joinable:
-                t1 = time.perf_counter()
-                self._write_back(batch, active, done)
-                self.seconds["write_back"] += time.perf_counter() - t1
-                for j in done:
-                    j.finished = t
-                    active.remove(j)
-                    footprint -= job_footprint_bytes(j.n_atoms)
-                changed = True
+            self.seconds["enqueue"] += time.perf_counter() - t1
+            while len(inflight) > 2 * self.depth:
+                retire(True)
+        retire(True)
         torch.cuda.synchronize()
+        if batch is not None:
+            status_dev.bitwise_or_(batch.status)
+        if int(status_dev.item()) != 0:
+            raise RuntimeError(f"device status {int(status_dev.item())} during serving")
+        totals = pairs_dev.cpu().numpy()
+        for j in jobs:
+            j.pairs = int(totals[index[id(j)]])
         return summarize(jobs)
 
 
@@ -241,9 +333,9 @@ def fifo_alone(jobs, alone_seconds):
             "pairs_per_s": pairs / float(sum(alone_seconds))}
 
 
-def time_alone(job: Job, mode) -> float:
+def time_alone(job: Job, mode, system=None) -> float:
     """Device time of the job run alone through md_step (state freshly loaded)."""
-    s = job.make_system()
+    s = system if system is not None else job.make_system()
     eng = api.Engine(s, mode=mode)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()

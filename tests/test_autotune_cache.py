@@ -59,3 +59,10 @@ def test_bad_cache_entries_are_remeasured(autotune, tmp_path, monkeypatch):
     e = autotune.tune(b, cache_path=str(path))
     assert e["measured"] and b.tuning == (3, 0)
     assert json.loads(path.read_text())[autotune.cache_key(b)]["tuning"] == [3, 0]
+
+
+def test_fixed_tile_tunes_over_the_cluster_shapes_only(autotune):
+    from paper_1611_04474_gb300 import api
+
+    assert autotune.shapes_for(api.ACCUM_FIXED_TILE) == [0, 5]
+    assert autotune.shapes_for(api.ACCUM_FIXED64) == list(range(api.BATCH_SHAPES))
