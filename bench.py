@@ -291,7 +291,7 @@ def measure_extras(eng, args):
     out["batch"] = b
     t0 = time.perf_counter()
     serve = {}
-    for rate, n in ((200.0, 150), (15.0, 80)):
+    for rate, n in ((200.0, 150), (15.0, 100)):
         r = run_serve.serve_window(rate, n, api.ACCUM_FIXED_TILE)
         keep = ("jobs", "latency_p50_s", "latency_p99_s", "pairs_per_s", "offered_jobs_per_s",
                 "achieved_jobs_per_s", "rebuilds", "ticks", "alone")

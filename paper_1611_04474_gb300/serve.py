@@ -70,7 +70,7 @@ class Server:
     def __init__(self, mode=api.ACCUM_FIXED_TILE, budget_bytes: int = 16 << 30,
                  tick_steps: int = 10, dt_fs: float = 1.0, device="cuda", lookahead: int = 32,
                  depth: int = 2, max_wait_s: float = 0.002, join_fraction: float = 0.2,
-                 active_atoms: int = 400_000, tick_ms: float = 4.0):
+                 active_atoms: int = 1_000_000, tick_ms: float = 4.0, done_ratio: float = 2.0):
         self.mode = mode
         self.budget = int(budget_bytes)
         self.tick = int(tick_steps)
@@ -87,11 +87,14 @@ class Server:
         # a tick runs about tick_ms of GPU time (at least tick_steps steps), so that the
         # host's work per tick stays small beside the GPU's
         self.tick_ms = float(tick_ms)
+        # finished jobs are dropped from the arena once their atoms reach this multiple
+        # of the live jobs' atoms (they are still stepped until then)
+        self.done_ratio = float(done_ratio)
         self.max_footprint = 0
         self.ticks = 0
         self.calls = 0
         self.rebuilds = 0
-        self.ms_per_step = None  # of the current arena, from its last completed tick
+        self.ms_per_atom_step = None  # GPU ms per atom-step, from the last completed tick
         # wall seconds of the serving loop by phase (host time; the GPU runs ahead)
         self.seconds = {"upload": 0.0, "rebuild": 0.0, "enqueue": 0.0, "wait": 0.0}
 
@@ -183,8 +186,8 @@ class Server:
                 t = now()
                 for j in done:
                     j.finished = t
-                if timing is not None and timing[2] is batch:  # (start event, steps, arena)
-                    self.ms_per_step = timing[0].elapsed_time(ev) / max(timing[1], 1)
+                if timing is not None and timing[1] > 0:  # (start event, steps, atoms)
+                    self.ms_per_atom_step = timing[0].elapsed_time(ev) / (timing[1] * max(timing[2], 1))
                 inflight.popleft()
                 block = False
 
@@ -232,7 +235,7 @@ class Server:
             rebuild = bool((not live and (waiting or members)) or (
                 waiting and (wait_atoms >= self.join_fraction * live_atoms
                              or now() - min(j.admitted for j in waiting) >= self.max_wait)) or (
-                members and done_atoms >= live_atoms) or (done_bytes and head_fits_after))
+                members and done_atoms >= self.done_ratio * live_atoms) or (done_bytes and head_fits_after))
             if rebuild:
                 t1 = time.perf_counter()
                 if batch is not None:
@@ -245,7 +248,6 @@ class Server:
                 footprint -= freed
                 if batch is not None:
                     batch.step(0)  # forces of the current positions
-                self.ms_per_step = None
                 self.rebuilds += 1
                 self.seconds["rebuild"] += time.perf_counter() - t1
                 continue
@@ -257,8 +259,9 @@ class Server:
             # one tick: md_batch_step calls split where live jobs take their last step
             t1 = time.perf_counter()
             left = self.tick
-            if self.ms_per_step:
-                left = max(self.tick, min(500, int(self.tick_ms / self.ms_per_step)))
+            arena_atoms = sum(j.n_atoms for j in members)  # finished jobs are stepped too
+            if self.ms_per_atom_step:
+                left = max(self.tick, min(500, int(self.tick_ms / (self.ms_per_atom_step * arena_atoms))))
             tick_steps = left
             ev0 = torch.cuda.Event(enable_timing=True)
             ev0.record()
@@ -287,7 +290,7 @@ class Server:
                     inflight.append((ev, done, None))
             ev = torch.cuda.Event(enable_timing=True)
             ev.record()
-            inflight.append((ev, [], (ev0, tick_steps - left, batch)))
+            inflight.append((ev, [], (ev0, tick_steps - left, arena_atoms)))
             self.ticks += 1
             self.seconds["enqueue"] += time.perf_counter() - t1
             while len(inflight) > 2 * self.depth:

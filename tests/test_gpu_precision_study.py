@@ -51,14 +51,41 @@ def _check_forces(api, s, ff, x, F, mode, rng, skip_window):
                 rms=float(np.sqrt((dF**2).sum() / (Fo**2).sum())))
 
 
-def test_precision_study_92k(cuda_lib):
-    api = cuda_lib
+def relaxed_control():
+    """The NVE control system: the gentle variant of the 92,224-atom lattice (sigma x 0.5,
+    masses 12-16 amu, Maxwell velocities at 300 K), its positions relaxed by 200 capped
+    steepest-descent steps of at most 0.01 A with the FP64 oracle's forces."""
+    from oracle import relax
+
     s = W.workload_lattice_92k().with_forcefield(0.5, (12.0, 16.0), seed=22)
+    ff = oracle.ForceField.from_system(s)
+    x = relax.steepest_descent(s.pos.astype(np.float64), s.q, s.type, s.box, ff,
+                               n_steps=200, max_step=0.01)
+    return W.System(s.name + "-relaxed", W.to_f32_in_box(x, s.box), s.q, s.type, s.box, s.rc,
+                    s.sigma, s.eps, s.AB, s.mass, s.vel, s.k_coulomb,
+                    dict(s.meta, relaxed="200 capped steepest-descent steps, 0.01 A, oracle"))
+
+
+def test_precision_study_92k(cuda_lib):
+    _study(cuda_lib, W.workload_lattice_92k().with_forcefield(0.5, (12.0, 16.0), seed=22),
+           "lattice_92224 (sigma x0.5, masses 12-16 amu)", "precision_study.json")
+
+
+def test_precision_study_relaxed_control_92k(cuda_lib):
+    """The same study from the relaxed start (SURVEY C10's control variant): the dynamics
+    stays near its starting temperature, so the drift measures the integration."""
+    report = _study(cuda_lib, relaxed_control(),
+                    "lattice_92224 relaxed (sigma x0.5, masses 12-16 amu, 200 SD steps)",
+                    "precision_study_relaxed.json")
+    d = {k: v["drift_kcal_per_mol_atom_per_ns"] for k, v in report["modes"].items()}
+    assert all(np.isfinite(v) for v in d.values()), d
+
+
+def _study(api, s, label, out_name):
     ff = oracle.ForceField.from_system(s)
     rng = np.random.default_rng(3)
     window = 16 * 2.0**-24 * s.rc * s.rc
-    report = {"system": "lattice_92224 (sigma x0.5, masses 12-16 amu)", "dt_fs": 1.0,
-              "steps": CHECK_STEPS[-1], "modes": {}}
+    report = {"system": label, "dt_fs": 1.0, "steps": CHECK_STEPS[-1], "modes": {}}
     names = {api.ACCUM_F32: "f32", api.ACCUM_FIXED64: "fixed64", api.ACCUM_F64: "f64"}
     hashes = []
     for mode in (api.ACCUM_F32, api.ACCUM_FIXED64, api.ACCUM_F64):
@@ -87,15 +114,19 @@ def test_precision_study_92k(cuda_lib):
             if run == 0:
                 t = np.arange(1, tot.shape[0] + 1, dtype=np.float64)
                 slope = np.polyfit(t, tot, 1)[0]  # kcal/mol per fs
+                k_b = 0.0019872043
                 report["modes"][names[mode]] = {
                     "force_checks": checks,
                     "E_total_start": float(tot[0]), "E_total_end": float(tot[-1]),
                     "drift_kcal_per_mol_atom_per_ns": float(slope * 1e6 / s.n),
-                    "KE_mean": float(e[:, 2].mean())}
+                    "E_total_rms_fluct_per_atom": float(np.std(tot - np.polyval(np.polyfit(t, tot, 1), t)) / s.n),
+                    "KE_mean": float(e[:, 2].mean()),
+                    "T_start_K": float(2 * e[0, 2] / (3 * s.n * k_b)),
+                    "T_end_K": float(2 * e[-1, 2] / (3 * s.n * k_b))}
     report["fixed64_sha256"] = hashes
     out = os.environ.get("MDNB_ARTIFACT_DIR")
     if out and os.path.isdir(out):
-        with open(os.path.join(out, "precision_study.json"), "w") as f:
+        with open(os.path.join(out, out_name), "w") as f:
             json.dump(report, f, indent=1)
     print(json.dumps(report, indent=1))
     assert len(set(hashes)) == 1, hashes
@@ -103,3 +134,4 @@ def test_precision_study_92k(cuda_lib):
         tol = 1e-12 if name == "f64" else 1e-5
         for k, c in m["force_checks"].items():
             assert c["max_norm"] <= tol, (name, k, c)
+    return report
