@@ -19,11 +19,12 @@ def main(argv=None):
     ap.add_argument("--n", type=int, default=W.APOA1_N, help="atoms of the lattice workload")
     ap.add_argument("--gas", action="store_true", help="the 3,000-atom random gas instead")
     ap.add_argument("--reps", type=int, default=3)
-    ap.add_argument("--mode", default="f32", choices=["f32", "fixed64", "f64"])
+    ap.add_argument("--mode", default="f32", choices=["f32", "fixed64", "f64", "fixed_tile"])
     ap.add_argument("--algo", type=int, default=0)
     ap.add_argument("--energy", action="store_true")
     args = ap.parse_args(argv)
-    mode = {"f32": api.ACCUM_F32, "fixed64": api.ACCUM_FIXED64, "f64": api.ACCUM_F64}[args.mode]
+    mode = {"f32": api.ACCUM_F32, "fixed64": api.ACCUM_FIXED64, "f64": api.ACCUM_F64,
+            "fixed_tile": api.ACCUM_FIXED_TILE}[args.mode]
     s = W.workload_random_3000() if args.gas else (
         W.workload_lattice_92k() if args.n == W.APOA1_N else W.lattice_box(n=args.n))
     eng = api.Engine(s, mode=mode, algo=args.algo)

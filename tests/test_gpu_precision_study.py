@@ -72,13 +72,19 @@ def test_precision_study_92k(cuda_lib):
 
 
 def test_precision_study_relaxed_control_92k(cuda_lib):
-    """The same study from the relaxed start (SURVEY C10's control variant): the dynamics
-    stays near its starting temperature, so the drift measures the integration."""
+    """The same study from the relaxed start (SURVEY C10's control variant).  The
+    relaxation lowers the potential energy and the heating, but the small LJ cores still
+    let opposite charges close in, so the drift mostly measures the 1 fs step against
+    those approaches; what is asserted is that the accumulation mode does not change it:
+    the drifts of FIXED64 and F32 lie within a factor 1.5 of the FP64 mode's."""
     report = _study(cuda_lib, relaxed_control(),
                     "lattice_92224 relaxed (sigma x0.5, masses 12-16 amu, 200 SD steps)",
                     "precision_study_relaxed.json")
     d = {k: v["drift_kcal_per_mol_atom_per_ns"] for k, v in report["modes"].items()}
     assert all(np.isfinite(v) for v in d.values()), d
+    for name in ("fixed64", "f32"):
+        ratio = d[name] / d["f64"]
+        assert 1 / 1.5 <= ratio <= 1.5, (name, d)
 
 
 def _study(api, s, label, out_name):
