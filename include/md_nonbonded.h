@@ -276,6 +276,25 @@ size_t md_batch_workspace_bytes(int32_t nsys, const md_system_desc *systems);
 int md_batch_prepare(int32_t nsys, const md_system_desc *systems, void *workspace,
                      size_t ws_bytes, void *stream);
 
+/* md_batch_prepare without waiting on the host.  md_batch_prepare copies the descriptors
+ * from memory it owns only for the duration of the call, so it waits for the stream to
+ * finish the copy (and everything enqueued before it).  A caller that keeps work queued
+ * on the stream while it rebuilds a batch (a server adding and removing systems between
+ * steps) passes a staging buffer instead:
+ *   host_staging  HOST memory of at least md_batch_staging_bytes(nsys, systems) bytes,
+ *                 16-byte aligned, owned by the caller; page-locked (cudaHostAlloc or an
+ *                 equivalent) so that the copy runs asynchronously.  The call writes the
+ *                 descriptors into it and enqueues one copy to the device on `stream`; the
+ *                 caller must not modify or free the buffer until that copy has completed
+ *                 (for example, until an event recorded on `stream` after the call has
+ *                 completed).
+ * Errors as md_batch_prepare; MD_ERR_INVALID_ARG for a missing, small or misaligned
+ * staging buffer. */
+size_t md_batch_staging_bytes(int32_t nsys, const md_system_desc *systems);
+int md_batch_prepare_staged(int32_t nsys, const md_system_desc *systems, void *workspace,
+                            size_t ws_bytes, void *host_staging, size_t staging_bytes,
+                            void *stream);
+
 /* md_step for a batch prepared in `workspace` with the same `systems` (host).  Arrays
  * are the concatenations described above; mode MD_ACCUM_F32, MD_ACCUM_FIXED64 or
  * MD_ACCUM_FIXED_TILE (the last with shapes 0 and 5 only, else MD_ERR_INVALID_ARG).

@@ -33,7 +33,8 @@ FIXED_SCALE = 2.0**32
 EXPORTS = ("md_strerror", "md_abi_version", "md_cell_dims", "md_workspace_bytes", "md_build_cells",
            "md_build_cells_noalloc", "md_nonbonded_forces", "md_nonbonded_forces_algo", "md_step",
            "md_verlet_workspace_bytes", "md_step_verlet",
-           "md_batch_workspace_bytes", "md_batch_prepare", "md_batch_step", "md_batch_step_tuned")
+           "md_batch_workspace_bytes", "md_batch_prepare", "md_batch_staging_bytes",
+           "md_batch_prepare_staged", "md_batch_step", "md_batch_step_tuned")
 BATCH_SHAPES = 6  # MD_BATCH_SHAPES: kernel shapes of the batched force launches
 
 _lib = None
@@ -96,6 +97,10 @@ def load(path: str | None = None):
     lib.md_batch_workspace_bytes.restype = sz
     lib.md_batch_prepare.argtypes = [i32, P, P, sz, P]
     lib.md_batch_prepare.restype = ctypes.c_int
+    lib.md_batch_staging_bytes.argtypes = [i32, P]
+    lib.md_batch_staging_bytes.restype = sz
+    lib.md_batch_prepare_staged.argtypes = [i32, P, P, sz, P, sz, P]
+    lib.md_batch_prepare_staged.restype = ctypes.c_int
     lib.md_batch_step.argtypes = [i32, P, P, P, P, i32, P, P, P, i32, f64, i32, P, P, sz, P, P]
     lib.md_batch_step.restype = ctypes.c_int
     lib.md_batch_step_tuned.argtypes = [i32, P, P, P, P, i32, P, P, P, i32, f64, i32, P, P, sz, P,
@@ -146,11 +151,30 @@ FORCE_DTYPE = {ACCUM_F32: torch.float32, ACCUM_FIXED64: torch.int64, ACCUM_F64: 
                ACCUM_FIXED_TILE: torch.int64}
 
 
+def to_device_async(a, dtype, device):
+    """A host array on `device` without a host wait: copied through page-locked memory
+    (the caching host allocator keeps that block until the copy has run)."""
+    t = torch.as_tensor(np.ascontiguousarray(np.asarray(a, dtype=dtype)))
+    if torch.device(device).type != "cuda":
+        return t.to(device)
+    return t.pin_memory().to(device, non_blocking=True)
+
+
+# page-locked staging buffers of md_batch_prepare_staged, each kept with an event recorded
+# after its copy until that event has completed
+_staging_in_flight = []
+
+
+def _keep_staging(buf, event):
+    _staging_in_flight[:] = [(b, e) for b, e in _staging_in_flight if not e.query()]
+    _staging_in_flight.append((buf, event))
+
+
 class ForceField:
     """Force-field constants on the device: AB float32 [T, T, 2], k, rc."""
 
     def __init__(self, AB, k_coulomb: float, rc: float, device="cuda"):
-        AB = torch.as_tensor(np.asarray(AB, dtype=np.float32)).to(device).contiguous()
+        AB = to_device_async(AB, np.float32, device).contiguous()
         if AB.dim() != 3 or AB.shape[0] != AB.shape[1] or AB.shape[2] != 2:
             raise ValueError("AB must be [T, T, 2]")
         self.AB = AB
@@ -346,6 +370,44 @@ class Engine:
              energy_log=energy_log, status=self.status, stream=stream)
         self.forces_valid = True
 
+    # ------------------------------------------------------------ checkpoints
+    def save_state(self, path: str):
+        """Write the MD state (positions, velocities, forces of the current mode, whether
+        they are valid) with the system's fingerprint to `path` (a numpy .npz); the
+        device is synchronised first."""
+        torch.cuda.synchronize(self.pos.device)
+        np.savez(path, pos=self.pos.cpu().numpy(), vel=self.vel.cpu().numpy(),
+                 forces=self.forces.cpu().numpy(), forces_valid=np.int32(self.forces_valid),
+                 mode=np.int32(self.mode), fingerprint=np.frombuffer(self.fingerprint(), np.uint8))
+
+    def load_state(self, path: str):
+        """Restore a state written by save_state for the same system and mode (raises
+        ValueError otherwise); the next step continues bit for bit where it left off."""
+        with np.load(path) as z:
+            if int(z["mode"]) != self.mode:
+                raise ValueError(f"checkpoint mode {int(z['mode'])} != engine mode {self.mode}")
+            if bytes(z["fingerprint"].tobytes()) != self.fingerprint():
+                raise ValueError("checkpoint belongs to another system")
+            for name in ("pos", "vel", "forces"):
+                t = getattr(self, name)
+                a = z[name]
+                if a.shape != tuple(t.shape) or a.dtype != np.dtype(str(t.dtype).replace("torch.", "")):
+                    raise ValueError(f"checkpoint {name} has shape {a.shape} / {a.dtype}")
+                t.copy_(torch.as_tensor(a))
+            self.forces_valid = bool(int(z["forces_valid"]))
+
+    def fingerprint(self) -> bytes:
+        """SHA-256 of what fixes the dynamics besides the state: charges, types, masses,
+        box, cutoff and the LJ table."""
+        import hashlib
+
+        s = self.system
+        h = hashlib.sha256()
+        for a in (s.q, s.type, s.inv_mass, np.asarray(self.box, np.float64), np.float64(s.rc),
+                  np.asarray(s.AB, np.float32), np.float64(s.k_coulomb)):
+            h.update(np.ascontiguousarray(a).tobytes())
+        return h.digest()
+
     def step_verlet(self, n_steps=1, dt_fs=1.0, skin=1.0, energy_log=None, stream=None):
         """md_step_verlet on this system's state; the number of cell builds accumulates in
         self.rebuilds (a device int64[1])."""
@@ -370,10 +432,12 @@ class Batch:
     batch without a host round trip; ``ffs`` likewise reuses device force fields.
     ``tuning`` = (shape for the systems with >= 3 cells per axis, shape for those with an
     axis of 2 cells), each in 0 .. BATCH_SHAPES-1 (md_batch_tuning); a performance choice
-    only, see ``autotune``."""
+    only, see ``autotune``.  ``staged`` prepares the batch through page-locked staging
+    memory (md_batch_prepare_staged) without waiting for the stream, for callers that keep
+    work queued on it; otherwise md_batch_prepare waits for the stream."""
 
     def __init__(self, systems, mode=ACCUM_FIXED64, device="cuda", state=None, ffs=None,
-                 tuning=(0, 0)):
+                 tuning=(0, 0), staged=False):
         if mode not in (ACCUM_F32, ACCUM_FIXED64, ACCUM_FIXED_TILE):
             raise ValueError("batched mode must be ACCUM_F32, ACCUM_FIXED64 or ACCUM_FIXED_TILE")
         self.systems = list(systems)
@@ -416,9 +480,19 @@ class Batch:
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=device)
         self.forces_valid = False
         self.tuning = tuple(tuning)
-        _check("md_batch_prepare", load().md_batch_prepare(
-            self.nsys, ctypes.byref(self.desc), _ptr(self.workspace), nbytes,
-            _stream(None)))
+        if staged:
+            sb = int(load().md_batch_staging_bytes(self.nsys, ctypes.byref(self.desc)))
+            buf = torch.empty(sb, dtype=torch.uint8, pin_memory=True)
+            _check("md_batch_prepare_staged", load().md_batch_prepare_staged(
+                self.nsys, ctypes.byref(self.desc), _ptr(self.workspace), nbytes,
+                ctypes.c_void_p(buf.data_ptr()), sb, _stream(None)))
+            ev = torch.cuda.Event()
+            ev.record()
+            _keep_staging(buf, ev)
+        else:
+            _check("md_batch_prepare", load().md_batch_prepare(
+                self.nsys, ctypes.byref(self.desc), _ptr(self.workspace), nbytes,
+                _stream(None)))
 
     def step(self, n_steps=1, dt_fs=1.0, count_pairs=False, stream=None):
         t = md_batch_tuning(int(self.tuning[0]), int(self.tuning[1]))

@@ -490,6 +490,42 @@ size_t md_batch_workspace_bytes(int32_t nsys, const md_system_desc *systems)
     return bl.total + kAlign;
 }
 
+// The batch's descriptor block (per-system SysDesc, cell -> system, the cell list of each
+// regime, atom -> system) filled into `host` with the device layout of bytes
+// [0, bl.run_base) of the batch workspace.
+static void fill_batch_block(int32_t nsys, const md_system_desc *systems, const BatchLayout &bl,
+                             const std::vector<int32_t> &dims, char *host)
+{
+    SysDesc *sys = reinterpret_cast<SysDesc *>(host + bl.sys);
+    int *cell_sys = reinterpret_cast<int *>(host + bl.cell_sys);
+    int *cell_list = reinterpret_cast<int *>(host + bl.cell_list);
+    int *atom_sys = reinterpret_cast<int *>(host + bl.atom_sys);
+    int atom = 0, cell = 0, reg = 0, mi = bl.ncell_reg;
+    for (int s = 0; s < nsys; ++s) {
+        const md_system_desc &d = systems[s];
+        SysDesc o;
+        memset(&o, 0, sizeof(o));
+        o.box = make_box(d.box_L, dims.data() + 3 * s);
+        o.AB = reinterpret_cast<const float2 *>(d.ff.AB);
+        o.ntypes = d.ff.ntypes;
+        o.kc = (float)d.ff.k_coulomb;
+        o.kc64 = d.ff.k_coulomb;
+        o.mi = half_shell_pairs_per_cell(o.box) == 27;
+        cutoff_thresholds(o.box, d.ff.rc, o.mi != 0, &o.rc2, &o.rc2m);
+        o.atom_offset = atom;
+        o.natoms = d.n;
+        o.cell_offset = cell;
+        memcpy(&sys[s], &o, sizeof(o));
+        for (int c = 0; c < o.box.ncell; ++c) {
+            cell_sys[(size_t)cell + c] = s;
+            cell_list[(size_t)(o.mi ? mi++ : reg++)] = cell + c;
+        }
+        for (int i = 0; i < d.n; ++i) atom_sys[(size_t)atom + i] = s;
+        atom += d.n;
+        cell += o.box.ncell;
+    }
+}
+
 int md_batch_prepare(int32_t nsys, const md_system_desc *systems, void *workspace, size_t ws_bytes,
                      void *stream)
 {
@@ -502,44 +538,41 @@ int md_batch_prepare(int32_t nsys, const md_system_desc *systems, void *workspac
     uintptr_t a = (p + kAlign - 1) & ~(uintptr_t)(kAlign - 1);
     if (ws_bytes < (a - p) + bl.total) return MD_ERR_WORKSPACE;
     char *wsp = reinterpret_cast<char *>(a);
-    std::vector<SysDesc> sys((size_t)nsys);
-    std::vector<int> cell_sys((size_t)bl.ncell), cell_list((size_t)bl.ncell), atom_sys((size_t)bl.n);
-    int atom = 0, cell = 0, reg = 0, mi = bl.ncell_reg;
-    for (int s = 0; s < nsys; ++s) {
-        const md_system_desc &d = systems[s];
-        SysDesc &o = sys[s];
-        o.box = make_box(d.box_L, dims.data() + 3 * s);
-        o.AB = reinterpret_cast<const float2 *>(d.ff.AB);
-        o.ntypes = d.ff.ntypes;
-        o.kc = (float)d.ff.k_coulomb;
-        o.kc64 = d.ff.k_coulomb;
-        o.mi = half_shell_pairs_per_cell(o.box) == 27;
-        cutoff_thresholds(o.box, d.ff.rc, o.mi != 0, &o.rc2, &o.rc2m);
-        o.atom_offset = atom;
-        o.natoms = d.n;
-        o.cell_offset = cell;
-        for (int c = 0; c < o.box.ncell; ++c) {
-            cell_sys[(size_t)cell + c] = s;
-            cell_list[(size_t)(o.mi ? mi++ : reg++)] = cell + c;
-        }
-        for (int i = 0; i < d.n; ++i) atom_sys[(size_t)atom + i] = s;
-        atom += d.n;
-        cell += o.box.ncell;
-    }
+    std::vector<char> host(bl.run_base);
+    fill_batch_block(nsys, systems, bl, dims, host.data());
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    cudaError_t ce = cudaMemcpyAsync(wsp + bl.sys, sys.data(), sizeof(SysDesc) * sys.size(),
-                                     cudaMemcpyHostToDevice, st);
-    if (ce == cudaSuccess)
-        ce = cudaMemcpyAsync(wsp + bl.cell_sys, cell_sys.data(), sizeof(int) * cell_sys.size(),
-                             cudaMemcpyHostToDevice, st);
-    if (ce == cudaSuccess)
-        ce = cudaMemcpyAsync(wsp + bl.cell_list, cell_list.data(), sizeof(int) * cell_list.size(),
-                             cudaMemcpyHostToDevice, st);
-    if (ce == cudaSuccess && bl.n > 0)
-        ce = cudaMemcpyAsync(wsp + bl.atom_sys, atom_sys.data(), sizeof(int) * atom_sys.size(),
-                             cudaMemcpyHostToDevice, st);
-    // the host vectors are released on return: wait for the copies to finish reading them
+    cudaError_t ce = cudaMemcpyAsync(wsp, host.data(), bl.run_base, cudaMemcpyHostToDevice, st);
+    // the host vector is released on return: wait for the copy to finish reading it
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    return ce == cudaSuccess ? MD_OK : MD_ERR_CUDA;
+}
+
+size_t md_batch_staging_bytes(int32_t nsys, const md_system_desc *systems)
+{
+    BatchLayout bl;
+    std::vector<int32_t> dims;
+    if (batch_layout(nsys, systems, &bl, &dims) != MD_OK) return 0;
+    return bl.run_base;
+}
+
+int md_batch_prepare_staged(int32_t nsys, const md_system_desc *systems, void *workspace,
+                            size_t ws_bytes, void *host_staging, size_t staging_bytes,
+                            void *stream)
+{
+    BatchLayout bl;
+    std::vector<int32_t> dims;
+    int e = batch_layout(nsys, systems, &bl, &dims);
+    if (e) return e;
+    if (!workspace) return MD_ERR_WORKSPACE;
+    uintptr_t p = reinterpret_cast<uintptr_t>(workspace);
+    uintptr_t a = (p + kAlign - 1) & ~(uintptr_t)(kAlign - 1);
+    if (ws_bytes < (a - p) + bl.total) return MD_ERR_WORKSPACE;
+    if (!host_staging || staging_bytes < bl.run_base) return MD_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(host_staging) & 15u) return MD_ERR_INVALID_ARG;
+    char *wsp = reinterpret_cast<char *>(a);
+    fill_batch_block(nsys, systems, bl, dims, static_cast<char *>(host_staging));
+    cudaError_t ce = cudaMemcpyAsync(wsp, host_staging, bl.run_base, cudaMemcpyHostToDevice,
+                                     static_cast<cudaStream_t>(stream));
     return ce == cudaSuccess ? MD_OK : MD_ERR_CUDA;
 }
 

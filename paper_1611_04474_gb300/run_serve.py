@@ -56,16 +56,19 @@ def main(argv=None):
     ap.add_argument("--mode", default="fixed_tile", choices=list(MODES))
     ap.add_argument("--active-atoms", type=int, default=None,
                     help="compute admission cap (atoms of live jobs in the arena)")
+    ap.add_argument("--depth", type=int, default=None, help="ticks enqueued ahead of the GPU")
+    ap.add_argument("--tick-ms", type=float, default=None, help="GPU time a tick aims for")
     args = ap.parse_args(argv)
     rates = [float(x) for x in args.rates.split(",")]
     sizes = [int(x) for x in args.jobs.split(",")]
     if len(sizes) == 1:
         sizes = sizes * len(rates)
     for rate, n in zip(rates, sizes):
-        kw = {} if args.active_atoms is None else {"active_atoms": args.active_atoms}
+        kw = {k: v for k, v in (("active_atoms", args.active_atoms), ("depth", args.depth),
+                                ("tick_ms", args.tick_ms)) if v is not None}
         res = serve_window(rate, n, MODES[args.mode], seed=args.seed, tick=args.tick,
                            budget_gb=args.budget_gb, **kw)
-        res["active_atoms"] = args.active_atoms
+        res.update(kw)
         res["mode"] = args.mode
         print(json.dumps(res), flush=True)
 

@@ -16,9 +16,13 @@ the deterministic modes (MD_ACCUM_FIXED_TILE, the default, and MD_ACCUM_FIXED64)
 recomputation gives the same bits, and a system's result never depends on the other
 systems of its batch, so a job's result is the same as running it alone.
 
-The host enqueues ticks ahead of the GPU (at most `depth` in flight) and learns of
-finished jobs from CUDA events; pair counts accumulate on the device and are read once
-at the end.
+The host enqueues ticks ahead of the GPU and learns of finished jobs from CUDA events;
+it waits only while more than 2 x `depth` events (ends of ticks and of jobs) are
+pending.  A deeper queue buys nothing once the GPU is busy and delays the next arrival,
+which joins behind every queued tick.  Nothing else in the loop waits for the stream: job
+uploads, batch descriptors and index lists go through page-locked memory
+(md_batch_prepare_staged for the descriptors).  Pair counts accumulate on the device and
+are read once at the end.
 
 Reported per run: job latencies (finish - arrival; p50, p99), the aggregate within-
 cutoff pair rate, the achieved against the offered job rate, and the largest
@@ -69,7 +73,7 @@ class Job:
 class Server:
     def __init__(self, mode=api.ACCUM_FIXED_TILE, budget_bytes: int = 16 << 30,
                  tick_steps: int = 10, dt_fs: float = 1.0, device="cuda", lookahead: int = 32,
-                 depth: int = 2, max_wait_s: float = 0.002, join_fraction: float = 0.2,
+                 depth: int = 1, max_wait_s: float = 0.002, join_fraction: float = 0.2,
                  active_atoms: int = 1_000_000, tick_ms: float = 4.0, done_ratio: float = 2.0):
         self.mode = mode
         self.budget = int(budget_bytes)
@@ -118,13 +122,14 @@ class Server:
         s = j.system
         j.ff = api.ForceField.from_system(s, self.device)
         d = self.device
+        up = api.to_device_async  # through page-locked memory: no wait for the stream
         j.state = {
-            "pos": torch.as_tensor(s.pos.astype(np.float64)).to(d, non_blocking=True),
-            "vel": torch.as_tensor(s.vel).to(d, non_blocking=True),
+            "pos": up(s.pos, np.float64, d),
+            "vel": up(s.vel, np.float64, d),
             "forces": torch.zeros((s.n, 3), dtype=api.FORCE_DTYPE[self.mode], device=d),
-            "q": torch.as_tensor(s.q).to(d, non_blocking=True),
-            "types": torch.as_tensor(s.type).to(d, non_blocking=True),
-            "inv_mass": torch.as_tensor(s.inv_mass).to(d, non_blocking=True),
+            "q": up(s.q, np.float32, d),
+            "types": up(s.type, np.int32, d),
+            "inv_mass": up(s.inv_mass, np.float32, d),
         }
         j.remaining = j.n_steps
 
@@ -139,7 +144,7 @@ class Server:
             return j.state[key] if k is None else getattr(prev, key)[prev.system_slice(k)]
         state = {key: torch.cat([src(j, key) for j in members]).contiguous() for key in keys}
         return api.Batch([j.system for j in members], mode=self.mode, device=self.device,
-                         state=state, ffs=[j.ff for j in members])
+                         state=state, ffs=[j.ff for j in members], staged=True)
 
     # ---------------------------------------------------------------- main loop
     def run(self, jobs, realtime: bool = True):
@@ -195,8 +200,8 @@ class Server:
             # add the arena's counts of `which` (members) to the jobs' totals, on the stream
             ks = [k for k, j in enumerate(mem) if any(j is x for x in which)]
             if ks:
-                sel = torch.tensor(ks, dtype=torch.int64, device=dev)
-                dst = torch.tensor([index[id(mem[k])] for k in ks], dtype=torch.int64, device=dev)
+                sel = api.to_device_async(ks, np.int64, dev)
+                dst = api.to_device_async([index[id(mem[k])] for k in ks], np.int64, dev)
                 pairs_dev.index_add_(0, dst, b.pair_count.index_select(0, sel))
 
         while pending or queue or waiting or any(j.remaining for j in members):
@@ -295,7 +300,8 @@ class Server:
             self.seconds["enqueue"] += time.perf_counter() - t1
             while len(inflight) > 2 * self.depth:
                 retire(True)
-        retire(True)
+        while inflight:
+            retire(True)
         torch.cuda.synchronize()
         if batch is not None:
             status_dev.bitwise_or_(batch.status)

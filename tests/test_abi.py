@@ -127,6 +127,45 @@ def test_fixed_tile_mode_only_on_the_cluster_kernel(lib):
                                        ctypes.byref(t), None) == -1
 
 
+def test_staged_batch_prepare_validation(lib):
+    from paper_1611_04474_gb300 import api
+
+    ff = api.md_forcefield(4, 0, 256, 332.0636, 3.0)
+    desc = (api.md_system_desc * 2)()
+    for k, (n, L) in enumerate(((10, 10.0), (40, 7.0))):
+        desc[k].n = n
+        for d in range(3):
+            desc[k].box_L[d] = L
+        desc[k].ff = ff
+    staging = int(lib.md_batch_staging_bytes(2, ctypes.byref(desc)))
+    ws = int(lib.md_batch_workspace_bytes(2, ctypes.byref(desc)))
+    # the staged block is the descriptor part of the workspace: per-system descriptors and
+    # one int per cell and per atom at least
+    assert 50 * 4 < staging < ws
+    bad = (api.md_system_desc * 1)()
+    bad[0].n = 10
+    for d in range(3):
+        bad[0].box_L[d] = 5.0  # rc at L/2
+    bad[0].ff = ff
+    assert lib.md_batch_staging_bytes(1, ctypes.byref(bad)) == 0
+    W = ctypes.c_void_p(256)  # never dereferenced: validation fails first
+    buf = (ctypes.c_uint8 * (staging + 32))()
+    base = ctypes.addressof(buf)
+    aligned = ctypes.c_void_p((base + 15) & ~15)
+    # missing or small workspace
+    assert lib.md_batch_prepare_staged(2, ctypes.byref(desc), None, ws, aligned, staging,
+                                       None) == -3
+    assert lib.md_batch_prepare_staged(2, ctypes.byref(desc), W, ws - 512, aligned, staging,
+                                       None) == -3
+    # missing, small or misaligned staging memory
+    assert lib.md_batch_prepare_staged(2, ctypes.byref(desc), W, ws, None, staging, None) == -1
+    assert lib.md_batch_prepare_staged(2, ctypes.byref(desc), W, ws, aligned, staging - 1,
+                                       None) == -1
+    odd = ctypes.c_void_p(aligned.value + 4)
+    assert lib.md_batch_prepare_staged(2, ctypes.byref(desc), W, ws, odd, staging, None) == -1
+    assert lib.md_batch_prepare_staged(1, ctypes.byref(bad), W, ws, aligned, staging, None) == -2
+
+
 def test_verlet_step_validation(lib):
     from paper_1611_04474_gb300 import api
 

@@ -180,3 +180,24 @@ def test_cuda_graph_replay_is_the_plain_loop(cuda_lib):
     assert int(graphed.status.item()) == 0
     for name in ("pos", "vel", "forces"):
         assert np.array_equal(getattr(graphed, name).cpu().numpy(), getattr(plain, name).cpu().numpy()), name
+
+
+def test_staged_prepare_behind_queued_work_is_the_plain_prepare(cuda_lib):
+    """md_batch_prepare_staged enqueues its copy without waiting for the stream: a batch
+    prepared that way while another batch's steps are still queued steps bit for bit like
+    one prepared with md_batch_prepare on an idle stream."""
+    api = cuda_lib
+    systems = _systems()
+    busy = api.Batch(W.batch_of_systems(nsys=4, seed=11, n_range=(20000, 40000)),
+                     mode=api.ACCUM_FIXED_TILE)
+    torch.cuda.synchronize()
+    results = []
+    for staged in (True, False):
+        busy.step(20, dt_fs=1.0)  # queued ahead of the prepare's copy
+        b = api.Batch(systems, mode=api.ACCUM_FIXED_TILE, staged=staged)
+        b.step(5, dt_fs=1.0, count_pairs=True)
+        torch.cuda.synchronize()
+        assert int(b.status.item()) == 0
+        results.append([t.cpu().numpy() for t in (b.pos, b.vel, b.forces, b.pair_count)])
+    for a, c in zip(*results):
+        assert np.array_equal(a, c)

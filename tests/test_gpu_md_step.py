@@ -205,3 +205,29 @@ def test_step_on_a_grid_of_more_than_1024_cells(cuda_lib):
     p = eng.pos.cpu().numpy().astype(np.float32)
     s1 = W.System(s.name, p, s.q, s.type, s.box, s.rc, s.sigma, s.eps, s.AB, s.mass, s.vel)
     assert np.array_equal(eng.forces.cpu().numpy(), reference(s1))
+
+
+def test_checkpoint_resume_is_bit_exact(cuda_lib, tmp_path):
+    """Save the state after 7 steps, restore it into a fresh engine, run 13 more: the
+    same bits as 20 steps in one run (FIXED64 and FIXED_TILE); a checkpoint of another
+    system or mode is refused."""
+    api = cuda_lib
+    s = W.lattice_box(n=3000, seed=6, ntypes=4).with_forcefield(0.5, (12.0, 16.0), seed=2)
+    for mode in (api.ACCUM_FIXED64, api.ACCUM_FIXED_TILE):
+        ref = api.Engine(s, mode=mode)
+        ref.step(20, dt_fs=1.0)
+        first = api.Engine(s, mode=mode)
+        first.step(7, dt_fs=1.0)
+        path = str(tmp_path / f"state_{mode}.npz")
+        first.save_state(path)
+        resumed = api.Engine(s, mode=mode)
+        resumed.load_state(path)
+        resumed.step(13, dt_fs=1.0)
+        torch.cuda.synchronize()
+        for a, b in zip(_state(ref), _state(resumed)):
+            assert np.array_equal(a, b)
+    other = W.lattice_box(n=3000, seed=7, ntypes=4).with_forcefield(0.5, (12.0, 16.0), seed=2)
+    with pytest.raises(ValueError):
+        api.Engine(other, mode=api.ACCUM_FIXED_TILE).load_state(path)
+    with pytest.raises(ValueError):
+        api.Engine(s, mode=api.ACCUM_F32).load_state(path)

@@ -27,6 +27,7 @@ def test_results_equal_alone_and_budget_respected(cuda_lib, mode):
     assert srv.max_footprint <= 2 * largest
     assert srv.rebuilds > 2  # jobs joined and left while others were running
     assert stats["latency_p99_s"] >= stats["latency_p50_s"] > 0
+    assert all(np.isfinite(j.finished) and j.finished > j.arrival for j in jobs)
     for j in jobs:
         eng = api.Engine(j.make_system(), mode=mode)
         eng.step(j.n_steps)
