@@ -795,6 +795,473 @@ k_cluster(CluArgs a, BatchArgs bt, unsigned long long *sys_pair_count, int *work
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Long-row form of the cluster-pair kernel (MD_ACCUM_F32, boxes with >= 3 cells per
+// axis, forces with or without the pair count).
+//
+// One CTA per (home cell, group of half-shell entries).  The group's cells (at most
+// kRowCells, each at most kRowCellAtoms atoms) are staged once, and every home cluster
+// of the cell is one row: its in-range neighbour clusters across all the group's cells,
+// four per warp step.  Lane (slot = lane / 8, neighbour atom jl = lane % 8) holds one
+// neighbour atom and evaluates it against all 8 home atoms, which every lane keeps in
+// registers as packed pairs of atoms.  The reaction on the neighbour atom is therefore
+// summed in registers (one vector reduction into the accumulator per step) and the home
+// sums stay in registers for the whole row (one reduction over the warp per row).  The
+// per-step overhead of the one-cluster-pair step is spread over 8 pairs a lane instead
+// of 2.  Cells with more atoms than a tile holds make the CTA run the one-cluster-pair
+// code for each of its group's entries instead.
+//
+// The displacement is formed exactly as in the one-cluster-pair form: neighbour tiles
+// staged with ns subtracted, home coordinates with hs subtracted, lo added to the
+// difference.  The group's cells are taken in classes of equal wrap code (equal hs, ns
+// and lo), each class one list per row.
+constexpr int kRW = 4;                 // warps per CTA
+constexpr int kRT = kRW * 32;
+constexpr int kRowCells = 4;           // cells per group at most
+constexpr int kRowCellAtoms = 256;     // atoms per cell at most (32 clusters)
+constexpr int kRowClu = kRowCells * (kRowCellAtoms / kCS);  // staged clusters at most
+constexpr int kRowDummy = kRowClu;     // a cluster of padding atoms, for partial steps
+constexpr int kRowSlots = (kRowClu + 1) * kCS;
+constexpr int kRowList = kRowClu + 8;  // diagonal entry + padding for the last step and the prefetch
+constexpr int kRowABStride = 5;        // float4 per neighbour type in a row's LJ table
+
+// Half-shell entries (0: the cell itself; j: forward neighbour j) of the four groups,
+// heaviest group first (about 840, 760, 760 and 510 cluster pairs in range at the
+// lattice density: face neighbours about 390, the cell itself 310, edges 185, corners 70).
+__constant__ int kRowGroup[4][kRowCells] = {{0, 1, 5, 7}, {3, 2, 4, -1}, {9, 6, 8, -1},
+                                            {10, 12, 11, 13}};
+constexpr int kRowGroups = 4;
+// slot of entry e in kPairOrder (the one-cluster-pair grid's blockIdx.y of that pair)
+__constant__ int kEntrySlot[14] = {3, 0, 4, 1, 5, 10, 6, 11, 7, 2, 8, 12, 9, 13};
+
+struct RowSmem {
+    float4 np[kRowSlots];                 // neighbour atoms (ns subtracted, q); padding -far
+    int ng[kRowSlots];                    // their slots in the accumulators; -1 for padding
+    float4 nlo[kRowClu], nhi[kRowClu];    // neighbour cluster boxes (padding excluded)
+    float4 hp[kRowCellAtoms];             // home atoms as stored; padding +far
+    float4 hlo[kRowCellAtoms / kCS], hhi[kRowCellAtoms / kCS];
+    unsigned short lst[kRW][kRowList];    // per-warp list of a row's clusters in range
+    unsigned char nt[kRowSlots];
+    unsigned char ht[kRowCellAtoms];
+    int ncl, nclass, self_nclu, next;
+    int cbeg[kRowCells + 1];              // first staged cluster of each cell (class order; unused cells empty)
+    int gbeg[kRowCells], gm[kRowCells];   // cell's first slot in the sorted arrays, atoms
+    int ccell[kRowCells + 1];             // first cell of each class
+    float chs[kRowCells][3], clo[kRowCells][3];  // hs and lo of each class
+};
+
+// Four neighbour clusters against the row's home cluster: this lane's neighbour atom ja
+// (position pj, type tj).  DIAG: the lane's cluster (slot 0) is the home cluster itself
+// (pairs with home atom k < jl only); SHIFT: the class adds lo to the difference.
+template <int STATS, bool DIAG, bool SHIFT>
+__device__ __forceinline__ void row_step(float4 *accum, const float4 *rab, int gs, const float4 &pj,
+                                         int tj, int slot, int jl, const f2 (&HX)[4],
+                                         const f2 (&HY)[4], const f2 (&HZ)[4], const f2 (&KQ)[4],
+                                         f2 (&FX)[4], f2 (&FY)[4], f2 (&FZ)[4], f2 LX, f2 LY,
+                                         f2 LZ, float rc2, unsigned &cnt)
+{
+    const float4 *ab = rab + tj * kRowABStride;
+    const f2 X = f2_dup(pj.x), Y = f2_dup(pj.y), Z = f2_dup(pj.z), Q = f2_dup(pj.w);
+    const unsigned dm = (DIAG && slot == 0) ? (1u << jl) - 1u : 0xffu;
+    f2 RX = 0ull, RY = 0ull, RZ = 0ull;
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        f2 dx = f2_sub(HX[p], X), dy = f2_sub(HY[p], Y), dz = f2_sub(HZ[p], Z);
+        if (SHIFT) {
+            dx = f2_add(dx, LX);
+            dy = f2_add(dy, LY);
+            dz = f2_add(dz, LZ);
+        }
+        const f2 r2 = f2_fma(dz, dz, f2_fma(dy, dy, f2_mul(dx, dx)));
+        float r2a, r2b;
+        f2_split(r2, r2a, r2b);
+        bool oka = r2a < rc2, okb = r2b < rc2;
+        if (DIAG) {
+            oka = oka && ((dm >> (2 * p)) & 1u);
+            okb = okb && ((dm >> (2 * p + 1)) & 1u);
+        }
+        const float4 t = ab[p];  // (A_a, A_b, -B_a, -B_b)
+        const f2 A = f2_make(t.x, t.y), nB = f2_make(t.z, t.w);
+        const f2 ir = f2_make(rsqrt_hw(r2a), rsqrt_hw(r2b));
+        const f2 ir2 = f2_mul(ir, ir);
+        const f2 ir6 = f2_mul(f2_mul(ir2, ir2), ir2);
+        const f2 ir8 = f2_mul(ir6, ir2);
+        const f2 lj = f2_mul(ir8, f2_fma(A, ir6, nB));
+        const f2 kqq = f2_mul(KQ[p], Q);
+        float fa, fb;
+        f2_split(f2_fma(f2_mul(kqq, ir2), ir, lj), fa, fb);
+        const f2 f = f2_make(oka ? fa : 0.0f, okb ? fb : 0.0f);
+        FX[p] = f2_fma(f, dx, FX[p]);
+        FY[p] = f2_fma(f, dy, FY[p]);
+        FZ[p] = f2_fma(f, dz, FZ[p]);
+        RX = f2_fma(f, dx, RX);
+        RY = f2_fma(f, dy, RY);
+        RZ = f2_fma(f, dz, RZ);
+        if (STATS >= kStatsCount) cnt += (unsigned)oka + (unsigned)okb;
+    }
+    // the reaction on the neighbour atom, added in L2 (a native vector reduction; shared
+    // memory has no native float add, and warps of the CTA meet the same atoms)
+    float a0, a1, b0, b1, c0, c1;
+    f2_split(RX, a0, a1);
+    f2_split(RY, b0, b1);
+    f2_split(RZ, c0, c1);
+    if (gs >= 0) red_add_v4(accum + gs, -(a0 + a1), -(b0 + b1), -(c0 + c1));
+}
+
+// The steps of one class list (padded with the dummy cluster to len + 7), each step's
+// neighbour atom loaded during the step before.
+template <int STATS, bool SHIFT>
+__device__ __forceinline__ void row_steps(RowSmem &sm, float4 *accum, const float4 *rab, const unsigned short *lst,
+                                          int len, bool diag, int lane, const f2 (&HX)[4],
+                                          const f2 (&HY)[4], const f2 (&HZ)[4], const f2 (&KQ)[4],
+                                          f2 (&FX)[4], f2 (&FY)[4], f2 (&FZ)[4], f2 LX, f2 LY,
+                                          f2 LZ, float rc2, unsigned &cnt)
+{
+    const int slot = lane >> 3, jl = lane & 7;
+    int ja = (int)lst[slot] * kCS + jl;
+    float4 pj = sm.np[ja];
+    int tj = sm.nt[ja], gs = sm.ng[ja];
+    int c0 = 0;
+    if (!SHIFT && diag) {
+        const int jn = (int)lst[4 + slot] * kCS + jl;
+        const float4 pn = sm.np[jn];
+        const int tn = sm.nt[jn], gn = sm.ng[jn];
+        row_step<STATS, true, false>(accum, rab, gs, pj, tj, slot, jl, HX, HY, HZ, KQ, FX, FY, FZ, LX, LY, LZ, rc2, cnt);
+        pj = pn;
+        tj = tn;
+        gs = gn;
+        c0 = 4;
+    }
+    for (; c0 < len; c0 += 4) {
+        const int jn = (int)lst[c0 + 4 + slot] * kCS + jl;
+        const float4 pn = sm.np[jn];
+        const int tn = sm.nt[jn], gn = sm.ng[jn];
+        row_step<STATS, false, SHIFT>(accum, rab, gs, pj, tj, slot, jl, HX, HY, HZ, KQ, FX, FY, FZ, LX, LY, LZ, rc2, cnt);
+        pj = pn;
+        tj = tn;
+        gs = gn;
+    }
+}
+
+template <int STATS>
+__device__ __forceinline__ void row_run(RowSmem &sm, const float2 *s_ab, float4 *rab, const CluArgs &a,
+                                        int ic, int mh, int hb, int lane, int T, float kc,
+                                        unsigned &cnt)
+{
+    unsigned short *lst = sm.lst[threadIdx.x >> 5];
+    // this row's LJ table: for each neighbour type, (A, A, -B, -B) of home atom pairs
+    for (int i = lane; i < T * 4; i += 32) {
+        const int tj = i >> 2, p = i & 3;
+        const float2 u = s_ab[sm.ht[ic * kCS + 2 * p] * T + tj];
+        const float2 v = s_ab[sm.ht[ic * kCS + 2 * p + 1] * T + tj];
+        rab[tj * kRowABStride + p] = make_float4(u.x, v.x, u.y, v.y);
+    }
+    const float4 *hp = sm.hp + ic * kCS;
+    f2 KQ[4], FX[4], FY[4], FZ[4], HX[4], HY[4], HZ[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        KQ[p] = f2_make(kc * hp[2 * p].w, kc * hp[2 * p + 1].w);
+        FX[p] = FY[p] = FZ[p] = 0ull;
+    }
+    const float4 bl = sm.hlo[ic], bh = sm.hhi[ic];
+    __syncwarp();
+    for (int c = 0; c < sm.nclass; ++c) {
+        // home coordinates with this class's hs subtracted (exact)
+        const float hx = sm.chs[c][0], hy = sm.chs[c][1], hz = sm.chs[c][2];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            const float4 u = hp[2 * p], v = hp[2 * p + 1];
+            HX[p] = f2_make(u.x - hx, v.x - hx);
+            HY[p] = f2_make(u.y - hy, v.y - hy);
+            HZ[p] = f2_make(u.z - hz, v.z - hz);
+        }
+        const float lx = sm.clo[c][0], ly = sm.clo[c][1], lz = sm.clo[c][2];
+        const bool shift = lx != 0.0f || ly != 0.0f || lz != 0.0f;
+        // the class's clusters in range (the box filter on the shifted home box)
+        const float blx = bl.x - hx, bly = bl.y - hy, blz = bl.z - hz;
+        const float bhx = bh.x - hx, bhy = bh.y - hy, bhz = bh.z - hz;
+        const bool diag = c == 0 && sm.self_nclu > 0;
+        const int jb0 = sm.cbeg[sm.ccell[c]], jb1 = sm.cbeg[sm.ccell[c + 1]];
+        int len = diag ? 1 : 0;
+        if (diag && lane == 0) lst[0] = (unsigned short)ic;
+        for (int jb = jb0; jb < jb1; jb += 32) {
+            const int jt = jb + lane;
+            bool in = false;
+            if (jt < jb1 && !(diag && jt <= ic)) {  // the cell itself: clusters after ic
+                const float4 nl = sm.nlo[jt], nh = sm.nhi[jt];
+                const float gx = fmaxf(0.f, fmaxf(blx - nh.x, nl.x - bhx));
+                const float gy = fmaxf(0.f, fmaxf(bly - nh.y, nl.y - bhy));
+                const float gz = fmaxf(0.f, fmaxf(blz - nh.z, nl.z - bhz));
+                in = gx * gx + gy * gy + gz * gz < a.rc2m;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, in);
+            if (in) lst[len + __popc(bal & ((1u << lane) - 1u))] = (unsigned short)jt;
+            len += __popc(bal);
+        }
+        // pad with the dummy cluster: to a multiple of 4, and one step more for the prefetch
+        if (lane < 7) lst[len + lane] = (unsigned short)kRowDummy;
+        __syncwarp();
+        const f2 LX = f2_dup(lx), LY = f2_dup(ly), LZ = f2_dup(lz);
+        if (shift)
+            row_steps<STATS, true>(sm, static_cast<float4 *>(a.accum), rab, lst, len, diag, lane, HX, HY, HZ, KQ, FX, FY, FZ, LX, LY, LZ, a.rc2, cnt);
+        else
+            row_steps<STATS, false>(sm, static_cast<float4 *>(a.accum), rab, lst, len, diag, lane, HX, HY, HZ, KQ, FX, FY, FZ, LX, LY, LZ, a.rc2, cnt);
+        __syncwarp();
+    }
+    // the 24 home sums (atom 2p and 2p + 1, x y z) over the warp: a reduce-scatter over the
+    // five lane bits, after which lane l < 24 holds sum l (atom l / 3, component l % 3)
+    float w[32];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        f2_split(FX[p], w[6 * p + 0], w[6 * p + 3]);
+        f2_split(FY[p], w[6 * p + 1], w[6 * p + 4]);
+        f2_split(FZ[p], w[6 * p + 2], w[6 * p + 5]);
+    }
+#pragma unroll
+    for (int q = 24; q < 32; ++q) w[q] = 0.0f;
+#pragma unroll
+    for (int half = 16; half >= 1; half >>= 1) {
+        const bool up = (lane & half) != 0;  // keep the upper half of the current values
+#pragma unroll
+        for (int q = 0; q < half; ++q) {
+            const float send = up ? w[q] : w[q + half];
+            const float keep = up ? w[q + half] : w[q];
+            w[q] = keep + __shfl_xor_sync(0xffffffffu, send, half);
+        }
+    }
+    // lane l's sum is value l when the bits of l select the kept halves: bit 4 of l chose
+    // the upper 16 values first, and so on down, so value index = l
+    if (lane < 24) {
+        const int ia = ic * kCS + lane / 3;
+        if (ia < mh)
+            atomicAdd(static_cast<float *>(a.accum) + 4 * (size_t)(hb + ia) + lane % 3, w[0]);
+    }
+}
+
+// One cell of a CTA's group (each thread forms them all itself, in registers).
+struct RowRec {
+    int key, code, beg, cnt, self;  // sort key: the cell itself, then no wrap, then by code
+    float hs[3], ns[3], lo[3];
+};
+constexpr int kStageIter = (kRowClu * kCS + kRT - 1) / kRT;  // neighbour slots per thread
+constexpr int kHomeIter = kRowCellAtoms / kRT;               // home slots per thread
+
+__device__ __forceinline__ int sel4(int k, int a0, int a1, int a2, int a3)
+{
+    return k == 0 ? a0 : k == 1 ? a1 : k == 2 ? a2 : a3;
+}
+__device__ __forceinline__ float sel4f(int k, float a0, float a1, float a2, float a3)
+{
+    return k == 0 ? a0 : k == 1 ? a1 : k == 2 ? a2 : a3;
+}
+
+template <int STATS>
+__global__ void __launch_bounds__(kRT, 4)
+k_cluster_rows(CluArgs a, int ncells)
+{
+    __shared__ __align__(16) union RowUnion {
+        RowSmem r;
+        CluSmem<MD_ACCUM_F32> c;
+    } u;
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    const int T = a.ntypes;
+    float2 *s_ab = reinterpret_cast<float2 *>(s_dyn);  // [T * T]: (A, -B)
+    float4 *s_rab = reinterpret_cast<float4 *>(s_dyn + ((sizeof(float2) * T * T + 15) & ~(size_t)15));
+    pdl_wait();
+    pdl_trigger();
+    const int cell = blockIdx.x, grp = blockIdx.y;
+    const int hb = a.cell_start[cell], mh = a.cell_start[cell + 1] - hb;
+    // the group's cells, sorted into classes of equal wrap code (the cell itself first)
+    RowRec r[kRowCells];
+    int ne = 0;
+#pragma unroll
+    for (int k = 0; k < kRowCells; ++k) {
+        const int e = kRowGroup[grp][k];
+        r[k].key = 1 << 20;
+        r[k].code = -1;
+        r[k].beg = r[k].cnt = r[k].self = 0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) r[k].hs[d] = r[k].ns[d] = r[k].lo[d] = 0.0f;
+        if (e >= 0) {
+            PairGeom q;
+            const int code = forward_pair(a.box, cell, e, q);
+            r[k].code = code;
+            r[k].self = q.self;
+            r[k].key = q.self ? -2 : (code == 13 ? -1 : code);
+            r[k].beg = a.cell_start[q.nbr];
+            r[k].cnt = a.cell_start[q.nbr + 1] - r[k].beg;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                r[k].hs[d] = q.hs[d];
+                r[k].ns[d] = q.ns[d];
+                r[k].lo[d] = q.lo[d];
+            }
+            ++ne;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < kRowCells - 1; ++i) {
+#pragma unroll
+        for (int j = 0; j < kRowCells - 1 - i; ++j) {
+            if (r[j].key > r[j + 1].key) {
+                const RowRec t = r[j];
+                r[j] = r[j + 1];
+                r[j + 1] = t;
+            }
+        }
+    }
+    bool fits = mh <= kRowCellAtoms;
+#pragma unroll
+    for (int k = 0; k < kRowCells; ++k) fits = fits && r[k].cnt <= kRowCellAtoms;
+    if (!fits) {
+        for (int k = 0; k < ne; ++k)
+            cluster_item<MD_ACCUM_F32, STATS, false, false>(u.c, s_ab, a, BatchArgs{}, nullptr, cell,
+                                                           kEntrySlot[kRowGroup[grp][k]], ncells);
+        return;
+    }
+    RowSmem &sm = u.r;
+    int cb[kRowCells + 1];
+    cb[0] = 0;
+#pragma unroll
+    for (int k = 0; k < kRowCells; ++k) cb[k + 1] = cb[k] + (r[k].cnt + kCS - 1) / kCS;
+    const int ncl = cb[kRowCells];
+    if (threadIdx.x == 0) {
+        int ncls = 0;
+#pragma unroll
+        for (int k = 0; k < kRowCells; ++k) {
+            if (k < ne && (k == 0 || r[k].code != r[k - 1].code)) {
+                sm.ccell[ncls] = k;
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    sm.chs[ncls][d] = r[k].hs[d];
+                    sm.clo[ncls][d] = r[k].lo[d];
+                }
+                ++ncls;
+            }
+            sm.gbeg[k] = r[k].beg;
+            sm.gm[k] = r[k].cnt;
+            sm.cbeg[k] = cb[k];
+        }
+        sm.cbeg[kRowCells] = ncl;
+        sm.ccell[ncls] = ne;
+        sm.nclass = ncls;
+        sm.ncl = ncl;
+        sm.self_nclu = r[0].self ? (mh + kCS - 1) / kCS : 0;
+        sm.next = kRW;
+    }
+    // every load of a thread (home and neighbour tiles) issued before its stores
+    float4 hv[kHomeIter];
+    int hty[kHomeIter];
+#pragma unroll
+    for (int i = 0; i < kHomeIter; ++i) {
+        const int t = threadIdx.x + i * kRT;
+        if (t < mh) {
+            hv[i] = a.pq[hb + t];
+            hty[i] = a.ty[hb + t];
+        }
+    }
+    float4 v[kStageIter];
+    int ty[kStageIter];
+    bool real[kStageIter];
+#pragma unroll
+    for (int i = 0; i < kStageIter; ++i) {
+        const int s = threadIdx.x + i * kRT;
+        const int k = (s >= cb[1] * kCS) + (s >= cb[2] * kCS) + (s >= cb[3] * kCS);
+        const int t = s - sel4(k, cb[0], cb[1], cb[2], cb[3]) * kCS;
+        real[i] = s < ncl * kCS && t < sel4(k, r[0].cnt, r[1].cnt, r[2].cnt, r[3].cnt);
+        if (real[i]) {
+            const int g = sel4(k, r[0].beg, r[1].beg, r[2].beg, r[3].beg) + t;
+            v[i] = a.pq[g];
+            ty[i] = a.ty[g];
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < kStageIter; ++i) {
+        const int s = threadIdx.x + i * kRT;
+        if (s < ncl * kCS) {
+            const int k = (s >= cb[1] * kCS) + (s >= cb[2] * kCS) + (s >= cb[3] * kCS);
+            float4 p = make_float4(-kFar, -kFar, -kFar, 0.f);
+            int tt = 0, g = -1;
+            if (real[i]) {  // ns subtracted (exact)
+                p = v[i];
+                p.x -= sel4f(k, r[0].ns[0], r[1].ns[0], r[2].ns[0], r[3].ns[0]);
+                p.y -= sel4f(k, r[0].ns[1], r[1].ns[1], r[2].ns[1], r[3].ns[1]);
+                p.z -= sel4f(k, r[0].ns[2], r[1].ns[2], r[2].ns[2], r[3].ns[2]);
+                tt = clamp_type(ty[i], T, a.status);
+                g = sel4(k, r[0].beg, r[1].beg, r[2].beg, r[3].beg) + s - sel4(k, cb[0], cb[1], cb[2], cb[3]) * kCS;
+            }
+            sm.np[s] = p;
+            sm.nt[s] = (unsigned char)tt;
+            sm.ng[s] = g;
+        }
+    }
+    for (int t = threadIdx.x; t < T * T; t += kRT) {
+        const float2 ab = a.AB[t];
+        s_ab[t] = make_float2(ab.x, -ab.y);
+    }
+    // home tile (as stored) and types; padding at +far
+    const int nic = (mh + kCS - 1) / kCS;
+#pragma unroll
+    for (int i = 0; i < kHomeIter; ++i) {
+        const int t = threadIdx.x + i * kRT;
+        if (t < nic * kCS) {
+            const bool hr = t < mh;
+            sm.hp[t] = hr ? hv[i] : make_float4(kFar, kFar, kFar, 0.f);
+            sm.ht[t] = (unsigned char)(hr ? clamp_type(hty[i], T, a.status) : 0);
+        }
+    }
+    if (threadIdx.x < kCS) {
+        const int s = kRowDummy * kCS + threadIdx.x;
+        sm.np[s] = make_float4(-kFar, -kFar, -kFar, 0.f);
+        sm.nt[s] = 0;
+        sm.ng[s] = -1;
+    }
+    __syncthreads();
+    // cluster boxes (padding excluded): home clusters, then the staged neighbour clusters
+    for (int k = threadIdx.x; k < nic + sm.ncl; k += kRT) {
+        const bool home = k < nic;
+        const int c = home ? k : k - nic;
+        const float4 *src = (home ? sm.hp : sm.np) + c * kCS;
+        float lo[3] = {kFar, kFar, kFar}, hi[3] = {-kFar, -kFar, -kFar};
+#pragma unroll
+        for (int t = 0; t < kCS; ++t) {
+            const float4 q = src[t];
+            if (fabsf(q.x) < kFar) {  // padding excluded
+                lo[0] = fminf(lo[0], q.x); hi[0] = fmaxf(hi[0], q.x);
+                lo[1] = fminf(lo[1], q.y); hi[1] = fmaxf(hi[1], q.y);
+                lo[2] = fminf(lo[2], q.z); hi[2] = fmaxf(hi[2], q.z);
+            }
+        }
+        const float4 l4 = make_float4(lo[0], lo[1], lo[2], 0.f), h4 = make_float4(hi[0], hi[1], hi[2], 0.f);
+        if (home) {
+            sm.hlo[c] = l4;
+            sm.hhi[c] = h4;
+        } else {
+            sm.nlo[c] = l4;
+            sm.nhi[c] = h4;
+        }
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float4 *rab = s_rab + (size_t)warp * T * kRowABStride;
+    unsigned cnt = 0;
+    for (int ic = warp; ic < nic;) {
+        row_run<STATS>(sm, s_ab, rab, a, ic, mh, hb, lane, T, a.kc, cnt);
+        int nx = 0;
+        if (lane == 0) nx = atomicAdd(&sm.next, 1);
+        ic = __shfl_sync(0xffffffffu, nx, 0);
+    }
+    if (STATS != kStatsNone) {
+        // the group's count in the partial of its first entry, zero in the others
+        Partial *partials = a.partials;
+        block_partial_to<kRT>(0.0, 0.0, 0.0, (unsigned long long)cnt,
+                              partials + (size_t)kEntrySlot[kRowGroup[grp][0]] * ncells + cell);
+        if (threadIdx.x == 0)
+            for (int k = 1; k < ne; ++k)
+                partials[(size_t)kEntrySlot[kRowGroup[grp][k]] * ncells + cell] = Partial{0.0, 0.0, 0.0, 0ull};
+    }
+}
+
 // Cluster-order accumulators -> forces_out in input order (slot s holds the atom
 // perm[corder[s]], or perm[s] without corder).  KICK: the half kick v += dt/2 a(F) of
 // that atom in the same pass, with the arithmetic of k_kick.
@@ -876,6 +1343,25 @@ cudaError_t launch_cluster_stats(int stats, const CluArgs &c, dim3 grid, cudaStr
     return launch_cluster_t<MODE, kStatsNone, false, MI, false, GATHER>(c, grid, stream);
 }
 
+// The long-row form: grid (cells, groups); partials in the one-cluster-pair grid's layout.
+cudaError_t launch_cluster_rows(int stats, const CluArgs &c, int ncells, cudaStream_t stream)
+{
+    const size_t dyn = ((sizeof(float2) * (size_t)c.ntypes * c.ntypes + 15) & ~(size_t)15) +
+                       sizeof(float4) * kRW * (size_t)c.ntypes * kRowABStride;
+    const size_t dyn_max = sizeof(float2) * kMaxTypes * kMaxTypes + sizeof(float4) * kRW * kMaxTypes * kRowABStride;
+    const dim3 grid(ncells, kRowGroups);
+    if (stats == kStatsCount) {
+        static const cudaError_t attr = cudaFuncSetAttribute(
+            k_cluster_rows<kStatsCount>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);
+        (void)attr;
+        return launch_pdl(k_cluster_rows<kStatsCount>, grid, dim3(kRT), dyn, stream, c, ncells);
+    }
+    static const cudaError_t attr = cudaFuncSetAttribute(
+        k_cluster_rows<kStatsNone>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);
+    (void)attr;
+    return launch_pdl(k_cluster_rows<kStatsNone>, grid, dim3(kRT), dyn, stream, c, ncells);
+}
+
 template <int MODE>
 cudaError_t launch_cluster_mode(bool mi, bool gather, int stats, const CluArgs &c, dim3 grid,
                                 cudaStream_t stream)
@@ -926,7 +1412,9 @@ cudaError_t launch_cluster(const ForceArgs &a, const WsLayout &ws, char *wsp, Pa
     if (gather && !a.presorted) return cudaErrorInvalidValue;
     dim3 grid(a.box.ncell, per_cell);
     const int stats = a.energy_virial_out ? kStatsEnergy : (a.pair_count_out ? kStatsCount : kStatsNone);
-    if (a.mode == MD_ACCUM_FIXED64)
+    if (a.mode == MD_ACCUM_F32 && !mi && !gather && stats != kStatsEnergy)
+        e = launch_cluster_rows(stats, c, a.box.ncell, stream);
+    else if (a.mode == MD_ACCUM_FIXED64)
         e = launch_cluster_mode<MD_ACCUM_FIXED64>(mi, gather, stats, c, grid, stream);
     else if (a.mode == MD_ACCUM_FIXED_TILE)
         e = launch_cluster_mode<MD_ACCUM_FIXED_TILE>(mi, gather, stats, c, grid, stream);

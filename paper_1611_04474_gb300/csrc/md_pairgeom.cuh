@@ -40,36 +40,52 @@ __device__ __forceinline__ bool small_box(const BoxF &b)
 // the cell itself, entry j >= 1 the forward neighbour kForward[j - 1].
 __constant__ int kPairOrder[14] = {1, 3, 9, 0, 2, 4, 6, 8, 10, 12, 5, 7, 11, 13};
 
+// Half-shell entry e (0: the cell itself, j >= 1: forward neighbour kForward[j - 1]) of
+// home cell c in a box with >= 3 cells per axis; returns the wrap code of the neighbour
+// (w_x + 3 w_y + 9 w_z + 13 with w_d in {-1, 0, 1} the face crossed along axis d; 13 for
+// none), which fixes hs, ns and lo.
+__device__ __forceinline__ int forward_pair(const BoxF &box, int c, int e, PairGeom &g)
+{
+    const int nx = box.dims[0], ny = box.dims[1];
+    const int cx = c % nx, cy = (c / nx) % ny, cz = c / (nx * ny);
+    g.home = c;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) g.hs[d] = g.ns[d] = g.lo[d] = 0.0f;
+    if (e == 0) {
+        g.nbr = c;
+        g.self = true;
+        return 13;
+    }
+    int t[3] = {cx + kForward[e - 1][0], cy + kForward[e - 1][1], cz + kForward[e - 1][2]};
+    int code = 13;
+#pragma unroll
+    for (int d = 0, m = 1; d < 3; ++d, m *= 3) {
+        int w = 0;
+        if (t[d] < 0) { t[d] += box.dims[d]; w = -1; }
+        else if (t[d] >= box.dims[d]) { t[d] -= box.dims[d]; w = 1; }
+        g.hs[d] = w > 0 ? box.Lhi[d] : 0.0f;
+        g.ns[d] = w < 0 ? box.Lhi[d] : 0.0f;
+        g.lo[d] = w > 0 ? -box.Llo[d] : (w < 0 ? box.Llo[d] : 0.0f);
+        code += w * m;
+    }
+    g.nbr = t[0] + nx * (t[1] + ny * t[2]);
+    g.self = false;
+    return code;
+}
+
 // Cell pair number k of home cell c; false if k names no pair.
 __device__ bool cell_pair(const BoxF &box, int c, int k, PairGeom &g)
 {
     const int nx = box.dims[0], ny = box.dims[1], nz = box.dims[2];
     const int cx = c % nx, cy = (c / nx) % ny, cz = c / (nx * ny);
+    if (!small_box(box)) {
+        if (k < 0 || k > 13) return false;
+        forward_pair(box, c, kPairOrder[k], g);
+        return true;
+    }
     g.home = c;
 #pragma unroll
     for (int d = 0; d < 3; ++d) g.hs[d] = g.ns[d] = g.lo[d] = 0.0f;
-    if (!small_box(box)) {
-        if (k < 0 || k > 13) return false;
-        k = kPairOrder[k];
-        if (k == 0) {
-            g.nbr = c;
-            g.self = true;
-            return true;
-        }
-        int t[3] = {cx + kForward[k - 1][0], cy + kForward[k - 1][1], cz + kForward[k - 1][2]};
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            int w = 0;
-            if (t[d] < 0) { t[d] += box.dims[d]; w = -1; }
-            else if (t[d] >= box.dims[d]) { t[d] -= box.dims[d]; w = 1; }
-            g.hs[d] = w > 0 ? box.Lhi[d] : 0.0f;
-            g.ns[d] = w < 0 ? box.Lhi[d] : 0.0f;
-            g.lo[d] = w > 0 ? -box.Llo[d] : (w < 0 ? box.Llo[d] : 0.0f);
-        }
-        g.nbr = t[0] + nx * (t[1] + ny * t[2]);
-        g.self = false;
-        return true;
-    }
     // small box: distinct cells of the 27-stencil, each unordered pair once (c' > c)
     if (k > 26) return false;
     auto cell_of = [&](int kk) {
