@@ -132,6 +132,7 @@ WsLayout ws_layout(int n, int ncell, bool bins, bool verlet)
     w.clu_pos_q = off;       off = align_up(off + sizeof(float4) * nn);
     w.clu_type = off;        off = align_up(off + sizeof(int32_t) * nn);
     w.clu_order = off;       off = align_up(off + sizeof(int32_t) * nn);
+    w.clu_box = off;         off = align_up(off + 2 * sizeof(float4) * nn);
     w.work = off;            off = align_up(off + 2 * sizeof(int32_t));
     w.bin_cap = bins && n > 0 ? bin_capacity(n, (int)nc) : 0;
     w.bins = off;            off = align_up(off + sizeof(int32_t) * nc * (size_t)w.bin_cap);
@@ -352,6 +353,7 @@ int md_step(double *pos, double *vel, void *forces, int32_t forces_valid, const 
     // then the forces with the second half kick in their last pass
     a.presorted = 1;
     a.accum_zeroed = mode != MD_ACCUM_F64;  // the build pass zeroes the accumulators
+    a.clu_box = reinterpret_cast<const float4 *>(wsp + ws.clu_box);  // written by the build
     a.kick_inv_mass = inv_mass;
     a.kick_half_dt = half_dt;
     auto build = [&](bool kick, double dt) -> cudaError_t {

@@ -337,7 +337,7 @@ k_sort_cluster(int *__restrict__ cell_start, const int *__restrict__ perm_tmp,
                const float4 *__restrict__ pos_q, const int32_t *__restrict__ type, BoxF box_in,
                BatchArgs b, int32_t *__restrict__ perm, float4 *__restrict__ pos_q_sorted,
                int32_t *__restrict__ type_sorted, const int *__restrict__ run_flag,
-               float4 *__restrict__ x_ref)
+               float4 *__restrict__ x_ref, float4 *__restrict__ clu_box)
 {
     __shared__ unsigned long long s_key[kClusterSortMax];  // by arrival
     __shared__ unsigned long long s_bkt[kClusterSortMax];  // grouped by column
@@ -382,6 +382,12 @@ k_sort_cluster(int *__restrict__ cell_start, const int *__restrict__ perm_tmp,
         m = cell_start[cg + 1] - s0;
     }
     if (m == 0) return;
+    // cluster boxes (clu_box): after the cell's atoms are written, from what was written
+    auto boxes = [&]() {
+        if (!clu_box) return;
+        __syncthreads();
+        write_cluster_boxes<kSortThreads>(pos_q_sorted, s0, m, clu_box, n);
+    };
     const int *mem = bin_cap ? bins + (size_t)cg * bin_cap : perm_tmp + s0;
     if (bin_cap && m > bin_cap) {
         // ordered gather: members in ascending input order, placed directly when the
@@ -411,7 +417,10 @@ k_sort_cluster(int *__restrict__ cell_start, const int *__restrict__ perm_tmp,
             found = total;
             __syncthreads();
         }
-        if (m > kClusterSortMax) return;
+        if (m > kClusterSortMax) {
+            boxes();
+            return;
+        }
         mem = list;
     } else if (m > kClusterSortMax) {
         // ascending input index, as k_cell_sort
@@ -430,6 +439,7 @@ k_sort_cluster(int *__restrict__ cell_start, const int *__restrict__ perm_tmp,
             }
             if (e >= 0) put(e, s0 + rank);
         }
+        boxes();
         return;
     }
     const int nx = box.dims[0], ny = box.dims[1];
@@ -492,6 +502,7 @@ k_sort_cluster(int *__restrict__ cell_start, const int *__restrict__ perm_tmp,
         type_sorted[slot] = s_typ[t];
         if (x_ref) x_ref[e] = s_pos[t];
     }
+    boxes();
 }
 
 }  // namespace
@@ -572,9 +583,9 @@ cudaError_t launch_kick_drift_build(double *pos, double *vel, const void *forces
         }
         // after the scatter, or straight after the build pass (programmatic launch)
         if (b)
-            e = launch_pdl(k_sort_cluster<true>, dim3(ncell), dim3(kSortThreads), 0, stream, cell_start, perm_tmp, bins, cap, (const int *)cell_id, n, sort_scans ? (const int *)cnt : nullptr, ncell, (const float4 *)pos_q, type, box_in, bb, perm, pos_q_sorted, type_sorted, (const int *)nullptr, (float4 *)nullptr);
+            e = launch_pdl(k_sort_cluster<true>, dim3(ncell), dim3(kSortThreads), 0, stream, cell_start, perm_tmp, bins, cap, (const int *)cell_id, n, sort_scans ? (const int *)cnt : nullptr, ncell, (const float4 *)pos_q, type, box_in, bb, perm, pos_q_sorted, type_sorted, (const int *)nullptr, (float4 *)nullptr, (float4 *)nullptr);
         else
-            e = launch_pdl(k_sort_cluster<false>, dim3(ncell), dim3(kSortThreads), 0, stream, cell_start, perm_tmp, bins, cap, (const int *)cell_id, n, sort_scans ? (const int *)cnt : nullptr, ncell, (const float4 *)pos_q, type, box_in, bb, perm, pos_q_sorted, type_sorted, (const int *)nullptr, (float4 *)nullptr);
+            e = launch_pdl(k_sort_cluster<false>, dim3(ncell), dim3(kSortThreads), 0, stream, cell_start, perm_tmp, bins, cap, (const int *)cell_id, n, sort_scans ? (const int *)cnt : nullptr, ncell, (const float4 *)pos_q, type, box_in, bb, perm, pos_q_sorted, type_sorted, (const int *)nullptr, (float4 *)nullptr, reinterpret_cast<float4 *>(wsp + ws.clu_box));
         if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
@@ -606,7 +617,8 @@ cudaError_t launch_verlet_rebuild(const float4 *pos_q, const int32_t *type, int 
     const BatchArgs nob = {};
     k_sort_cluster<false><<<box.ncell, kSortThreads, 0, stream>>>(
         cell_start, perm_tmp, (const int *)nullptr, 0, (const int *)cell_id, n, (const int *)nullptr,
-        box.ncell, pos_q, type, box, nob, perm, pos_q_sorted, type_sorted, run_flag, x_ref);
+        box.ncell, pos_q, type, box, nob, perm, pos_q_sorted, type_sorted, run_flag, x_ref,
+        (float4 *)nullptr);
     return cudaGetLastError();
 }
 

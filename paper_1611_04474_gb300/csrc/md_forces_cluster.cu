@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(kOrderThreads)
 k_cluster_order(const int32_t *__restrict__ cell_start, const float4 *__restrict__ pq,
                 const int32_t *__restrict__ ty, BoxF box, float4 *__restrict__ cpq,
                 int32_t *__restrict__ cty, int32_t *__restrict__ corder, void *__restrict__ accum,
-                int mode, int n)
+                int mode, int n, float4 *__restrict__ cbox)
 {
     __shared__ unsigned long long s_key[kSortMax];  // by sorted slot
     __shared__ unsigned long long s_bkt[kSortMax];  // grouped by column
@@ -91,6 +91,8 @@ k_cluster_order(const int32_t *__restrict__ cell_start, const float4 *__restrict
             cpq[b + t] = pq[b + t];
             cty[b + t] = ty[b + t];
         }
+        __syncthreads();
+        write_cluster_boxes<kOrderThreads>(cpq, b, m, cbox, n);
         return;
     }
     const int nx = box.dims[0], ny = box.dims[1];
@@ -145,6 +147,8 @@ k_cluster_order(const int32_t *__restrict__ cell_start, const float4 *__restrict
         cpq[b + rank] = pq[b + t];
         cty[b + rank] = ty[b + t];
     }
+    __syncthreads();
+    write_cluster_boxes<kOrderThreads>(cpq, b, m, cbox, n);
 }
 
 // Packed pairs of FP32 values (element 0 in the low half).
@@ -191,6 +195,8 @@ struct CluArgs {
     // (input order, wrapped in FP64 and rounded to float)
     const float4 *gpq;
     const int32_t *perm;
+    // cluster boxes of the cluster-ordered arrays (long-row form), or null
+    const float4 *cbox;
 };
 
 // Bounding boxes of the clusters of a staged tile (padding excluded).
@@ -1043,17 +1049,8 @@ struct RowRec {
     int key, code, beg, cnt, self;  // sort key: the cell itself, then no wrap, then by code
     float hs[3], ns[3], lo[3];
 };
-constexpr int kStageIter = (kRowClu * kCS + kRT - 1) / kRT;  // neighbour slots per thread
 constexpr int kHomeIter = kRowCellAtoms / kRT;               // home slots per thread
 
-__device__ __forceinline__ int sel4(int k, int a0, int a1, int a2, int a3)
-{
-    return k == 0 ? a0 : k == 1 ? a1 : k == 2 ? a2 : a3;
-}
-__device__ __forceinline__ float sel4f(int k, float a0, float a1, float a2, float a3)
-{
-    return k == 0 ? a0 : k == 1 ? a1 : k == 2 ? a2 : a3;
-}
 
 template <int STATS>
 __global__ void __launch_bounds__(kRT, 4)
@@ -1149,7 +1146,13 @@ k_cluster_rows(CluArgs a, int ncells)
         sm.self_nclu = r[0].self ? (mh + kCS - 1) / kCS : 0;
         sm.next = kRW;
     }
-    // every load of a thread (home and neighbour tiles) issued before its stores
+    for (int t = threadIdx.x; t < T * T; t += kRT) {
+        const float2 ab = a.AB[t];
+        s_ab[t] = make_float2(ab.x, -ab.y);
+    }
+    // every load of a thread (home and neighbour tiles, cluster boxes) issued before its
+    // stores: at most 256 atoms (32 clusters) per cell, so two slots of each cell and one
+    // cluster of each cell per thread
     float4 hv[kHomeIter];
     int hty[kHomeIter];
 #pragma unroll
@@ -1160,47 +1163,30 @@ k_cluster_rows(CluArgs a, int ncells)
             hty[i] = a.ty[hb + t];
         }
     }
-    float4 v[kStageIter];
-    int ty[kStageIter];
-    bool real[kStageIter];
-#pragma unroll
-    for (int i = 0; i < kStageIter; ++i) {
-        const int s = threadIdx.x + i * kRT;
-        const int k = (s >= cb[1] * kCS) + (s >= cb[2] * kCS) + (s >= cb[3] * kCS);
-        const int t = s - sel4(k, cb[0], cb[1], cb[2], cb[3]) * kCS;
-        real[i] = s < ncl * kCS && t < sel4(k, r[0].cnt, r[1].cnt, r[2].cnt, r[3].cnt);
-        if (real[i]) {
-            const int g = sel4(k, r[0].beg, r[1].beg, r[2].beg, r[3].beg) + t;
-            v[i] = a.pq[g];
-            ty[i] = a.ty[g];
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < kStageIter; ++i) {
-        const int s = threadIdx.x + i * kRT;
-        if (s < ncl * kCS) {
-            const int k = (s >= cb[1] * kCS) + (s >= cb[2] * kCS) + (s >= cb[3] * kCS);
-            float4 p = make_float4(-kFar, -kFar, -kFar, 0.f);
-            int tt = 0, g = -1;
-            if (real[i]) {  // ns subtracted (exact)
-                p = v[i];
-                p.x -= sel4f(k, r[0].ns[0], r[1].ns[0], r[2].ns[0], r[3].ns[0]);
-                p.y -= sel4f(k, r[0].ns[1], r[1].ns[1], r[2].ns[1], r[3].ns[1]);
-                p.z -= sel4f(k, r[0].ns[2], r[1].ns[2], r[2].ns[2], r[3].ns[2]);
-                tt = clamp_type(ty[i], T, a.status);
-                g = sel4(k, r[0].beg, r[1].beg, r[2].beg, r[3].beg) + s - sel4(k, cb[0], cb[1], cb[2], cb[3]) * kCS;
-            }
-            sm.np[s] = p;
-            sm.nt[s] = (unsigned char)tt;
-            sm.ng[s] = g;
-        }
-    }
-    for (int t = threadIdx.x; t < T * T; t += kRT) {
-        const float2 ab = a.AB[t];
-        s_ab[t] = make_float2(ab.x, -ab.y);
-    }
-    // home tile (as stored) and types; padding at +far
     const int nic = (mh + kCS - 1) / kCS;
+    float4 hbl, hbh;
+    if (threadIdx.x < nic) {
+        hbl = a.cbox[hb + threadIdx.x * kCS];
+        hbh = a.cbox[(size_t)a.n + hb + threadIdx.x * kCS];
+    }
+    float4 v[kRowCells][2], bl[kRowCells], bh[kRowCells];
+    int ty[kRowCells][2];
+#pragma unroll
+    for (int k = 0; k < kRowCells; ++k) {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int t = threadIdx.x + i * kRT;
+            if (t < r[k].cnt) {
+                v[k][i] = a.pq[r[k].beg + t];
+                ty[k][i] = a.ty[r[k].beg + t];
+            }
+        }
+        if (threadIdx.x * kCS < r[k].cnt) {
+            bl[k] = a.cbox[r[k].beg + threadIdx.x * kCS];
+            bh[k] = a.cbox[(size_t)a.n + r[k].beg + threadIdx.x * kCS];
+        }
+    }
+    // home tile (as stored) and types, padding at +far; home cluster boxes
 #pragma unroll
     for (int i = 0; i < kHomeIter; ++i) {
         const int t = threadIdx.x + i * kRT;
@@ -1210,36 +1196,44 @@ k_cluster_rows(CluArgs a, int ncells)
             sm.ht[t] = (unsigned char)(hr ? clamp_type(hty[i], T, a.status) : 0);
         }
     }
+    if (threadIdx.x < nic) {
+        sm.hlo[threadIdx.x] = hbl;
+        sm.hhi[threadIdx.x] = hbh;
+    }
+    // neighbour tiles in class order, ns subtracted (exact), padding at -far; their boxes
+    // moved by the same shift
+#pragma unroll
+    for (int k = 0; k < kRowCells; ++k) {
+        const int s0 = cb[k] * kCS, span = (cb[k + 1] - cb[k]) * kCS;
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int t = threadIdx.x + i * kRT;
+            if (t < span) {
+                float4 p = make_float4(-kFar, -kFar, -kFar, 0.f);
+                int tt = 0;
+                if (t < r[k].cnt) {
+                    p = v[k][i];
+                    p.x -= r[k].ns[0];
+                    p.y -= r[k].ns[1];
+                    p.z -= r[k].ns[2];
+                    tt = clamp_type(ty[k][i], T, a.status);
+                }
+                sm.np[s0 + t] = p;
+                sm.nt[s0 + t] = (unsigned char)tt;
+                sm.ng[s0 + t] = t < r[k].cnt ? r[k].beg + t : -1;
+            }
+        }
+        if (threadIdx.x * kCS < r[k].cnt) {
+            const int c = cb[k] + threadIdx.x;
+            sm.nlo[c] = make_float4(bl[k].x - r[k].ns[0], bl[k].y - r[k].ns[1], bl[k].z - r[k].ns[2], 0.f);
+            sm.nhi[c] = make_float4(bh[k].x - r[k].ns[0], bh[k].y - r[k].ns[1], bh[k].z - r[k].ns[2], 0.f);
+        }
+    }
     if (threadIdx.x < kCS) {
         const int s = kRowDummy * kCS + threadIdx.x;
         sm.np[s] = make_float4(-kFar, -kFar, -kFar, 0.f);
         sm.nt[s] = 0;
         sm.ng[s] = -1;
-    }
-    __syncthreads();
-    // cluster boxes (padding excluded): home clusters, then the staged neighbour clusters
-    for (int k = threadIdx.x; k < nic + sm.ncl; k += kRT) {
-        const bool home = k < nic;
-        const int c = home ? k : k - nic;
-        const float4 *src = (home ? sm.hp : sm.np) + c * kCS;
-        float lo[3] = {kFar, kFar, kFar}, hi[3] = {-kFar, -kFar, -kFar};
-#pragma unroll
-        for (int t = 0; t < kCS; ++t) {
-            const float4 q = src[t];
-            if (fabsf(q.x) < kFar) {  // padding excluded
-                lo[0] = fminf(lo[0], q.x); hi[0] = fmaxf(hi[0], q.x);
-                lo[1] = fminf(lo[1], q.y); hi[1] = fmaxf(hi[1], q.y);
-                lo[2] = fminf(lo[2], q.z); hi[2] = fmaxf(hi[2], q.z);
-            }
-        }
-        const float4 l4 = make_float4(lo[0], lo[1], lo[2], 0.f), h4 = make_float4(hi[0], hi[1], hi[2], 0.f);
-        if (home) {
-            sm.hlo[c] = l4;
-            sm.hhi[c] = h4;
-        } else {
-            sm.nlo[c] = l4;
-            sm.nhi[c] = h4;
-        }
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1383,6 +1377,7 @@ cudaError_t launch_cluster(const ForceArgs &a, const WsLayout &ws, char *wsp, Pa
     float4 *cpq = reinterpret_cast<float4 *>(wsp + ws.clu_pos_q);
     int32_t *cty = reinterpret_cast<int32_t *>(wsp + ws.clu_type);
     int32_t *corder = reinterpret_cast<int32_t *>(wsp + ws.clu_order);
+    float4 *cbox = reinterpret_cast<float4 *>(wsp + ws.clu_box);
     // the MD step's build pass, or else the ordering pass, zeroes the accumulators; a
     // presorted call without that needs the memset
     cudaError_t e = a.accum_zeroed || !a.presorted ? cudaSuccess : cudaMemsetAsync(accum, 0, acc_bytes, stream);
@@ -1390,7 +1385,7 @@ cudaError_t launch_cluster(const ForceArgs &a, const WsLayout &ws, char *wsp, Pa
     if (!a.presorted)
         k_cluster_order<<<a.box.ncell, kOrderThreads, 0, stream>>>(a.cell_start, a.pos_q_sorted,
                                                                    a.type_sorted, a.box, cpq, cty, corder,
-                                                                   accum, a.mode, a.n);
+                                                                   accum, a.mode, a.n, cbox);
     CluArgs c;
     c.cell_start = a.cell_start;
     c.pq = a.presorted ? a.pos_q_sorted : cpq;
@@ -1408,11 +1403,13 @@ cudaError_t launch_cluster(const ForceArgs &a, const WsLayout &ws, char *wsp, Pa
     c.status = a.status;
     c.gpq = a.gather_pq;
     c.perm = a.perm;
+    c.cbox = a.presorted ? a.clu_box : cbox;
     const bool gather = a.gather_pq != nullptr;
     if (gather && !a.presorted) return cudaErrorInvalidValue;
     dim3 grid(a.box.ncell, per_cell);
     const int stats = a.energy_virial_out ? kStatsEnergy : (a.pair_count_out ? kStatsCount : kStatsNone);
-    if (a.mode == MD_ACCUM_F32 && !mi && !gather && stats != kStatsEnergy)
+    // (its list entries pack a slot into 28 bits)
+    if (a.mode == MD_ACCUM_F32 && !mi && !gather && stats != kStatsEnergy && c.cbox && a.n < (1 << 28))
         e = launch_cluster_rows(stats, c, a.box.ncell, stream);
     else if (a.mode == MD_ACCUM_FIXED64)
         e = launch_cluster_mode<MD_ACCUM_FIXED64>(mi, gather, stats, c, grid, stream);

@@ -72,6 +72,7 @@ struct WsLayout {
     size_t ev;          // double[4]          energy/virial scratch of md_step
     size_t st_cell_start, st_perm, st_pos_q_sorted, st_type_sorted, st_pos_q;  // md_step only
     size_t clu_pos_q, clu_type, clu_order;  // cluster-pair kernel: per-cell reordered copies
+    size_t clu_box;     // float4 [2 n]  cluster boxes: lo at the cluster's first slot, hi at n + it
     size_t work;        // int[2] item counters of persistent force launches
     size_t bins;        // int32 [ncell][bin_cap] members of each cell by arrival (MD step)
     size_t v_ref;       // float4 [n]  positions at the last cell rebuild (Verlet step only)
@@ -362,6 +363,27 @@ __device__ __forceinline__ T warp_sum(T v)
     return v;
 }
 
+// Bounding boxes of the clusters (8 consecutive slots) of one cell whose m atoms start at
+// slot s0 of p, in the cell's final order: lo at box[first slot], hi at box[n + first
+// slot]; the last cluster's empty slots are left out.  The cell's atoms must have been
+// written before (the caller synchronises its block first).
+template <int NT>
+__device__ __forceinline__ void write_cluster_boxes(const float4 *p, int s0, int m, float4 *box, int n)
+{
+    for (int k = threadIdx.x; 8 * k < m; k += NT) {
+        const int b = s0 + 8 * k, e = min(m - 8 * k, 8);
+        float4 lo = p[b], hi = lo;
+        for (int t = 1; t < e; ++t) {
+            const float4 q = p[b + t];
+            lo.x = fminf(lo.x, q.x); hi.x = fmaxf(hi.x, q.x);
+            lo.y = fminf(lo.y, q.y); hi.y = fmaxf(hi.y, q.y);
+            lo.z = fminf(lo.z, q.z); hi.z = fmaxf(hi.z, q.z);
+        }
+        box[b] = lo;
+        box[(size_t)n + b] = hi;
+    }
+}
+
 // Sum (e_lj, e_c, w, count) over the block into *slot in a fixed order.
 template <int kThreads>
 __device__ __forceinline__ void block_partial_to(double e_lj, double e_c, double w,
@@ -435,6 +457,9 @@ struct ForceArgs {
     // the build pass of the MD step already zeroed the cluster-order accumulators (and
     // the persistent launches' item counters)
     int accum_zeroed = 0;
+    // bounding boxes of the presorted cells' clusters (lo at the first slot of a cluster, hi
+    // at n + that slot), written by the MD step's build; null where none were written
+    const float4 *clu_box = nullptr;
     // Verlet step: the cells (cell_start, perm, type_sorted) are those of the last rebuild
     // and the current positions come from this input-order float copy through perm
     const float4 *gather_pq = nullptr;

@@ -144,6 +144,27 @@ def test_forces_match_oracle(cuda_lib, name, mode):
             assert abs(ev[k] - ref.energy[k]) <= etol * ref.energy_abs[k] + 1e-9, (k, ev, ref.energy)
 
 
+@pytest.mark.parametrize("name", list(SYSTEMS))
+@pytest.mark.parametrize("count", [False, True])
+def test_f32_forces_without_energies_match_oracle(cuda_lib, name, count):
+    """The FP32 force call without energies (the long-row form of the cluster kernel on
+    boxes with >= 3 cells per axis), with and without the pair count, against the oracle;
+    run twice so that nothing depends on what an earlier kernel left in shared memory."""
+    api = cuda_lib
+    s, ff, p, ref, alts, nb = ref_for(name)
+    for _ in range(2):
+        eng = api.Engine(s, mode=api.ACCUM_F32, algo=api.ALGO_CLUSTER)
+        eng.build_cells()
+        eng.compute_forces(energy=False, count=count)
+        torch.cuda.synchronize()
+        assert int(eng.status.item()) == 0
+        F = api.forces_to_f64(eng.forces, api.ACCUM_F32).cpu().numpy()
+        err = force_errors(F, ref.F, ref.cond, alts)
+        assert err["max_norm"] <= TOL_F32, (name, count, err, nb)
+        if count:
+            assert abs(int(eng.pair_count.item()) - ref.npairs) <= nb
+
+
 @pytest.mark.parametrize("name", ["gas3000", "lattice3000"])
 def test_fixed_mode_exact_sum_and_reproducible(cuda_lib, name):
     api = cuda_lib
