@@ -1337,6 +1337,20 @@ cudaError_t launch_cluster_stats(int stats, const CluArgs &c, dim3 grid, cudaStr
     return launch_cluster_t<MODE, kStatsNone, false, MI, false, GATHER>(c, grid, stream);
 }
 
+// SMs of the current device (host query, cached per device).
+int device_sms()
+{
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    if (!cached[dev]) {
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cached[dev] = sms > 0 ? sms : 1;
+    }
+    return cached[dev];
+}
+
 // The long-row form: grid (cells, groups); partials in the one-cluster-pair grid's layout.
 cudaError_t launch_cluster_rows(int stats, const CluArgs &c, int ncells, cudaStream_t stream)
 {
@@ -1408,8 +1422,11 @@ cudaError_t launch_cluster(const ForceArgs &a, const WsLayout &ws, char *wsp, Pa
     if (gather && !a.presorted) return cudaErrorInvalidValue;
     dim3 grid(a.box.ncell, per_cell);
     const int stats = a.energy_virial_out ? kStatsEnergy : (a.pair_count_out ? kStatsCount : kStatsNone);
-    // (its list entries pack a slot into 28 bits)
-    if (a.mode == MD_ACCUM_F32 && !mi && !gather && stats != kStatsEnergy && c.cbox && a.n < (1 << 28))
+    // the long-row form where its grid (4 CTAs a cell) fills at least two waves of 4 CTAs
+    // per SM; smaller grids leave SMs idle, and the one-cluster-pair grid (14 a cell) is
+    // faster there
+    if (a.mode == MD_ACCUM_F32 && !mi && !gather && stats != kStatsEnergy && c.cbox &&
+        (long long)a.box.ncell * kRowGroups >= 8LL * device_sms())
         e = launch_cluster_rows(stats, c, a.box.ncell, stream);
     else if (a.mode == MD_ACCUM_FIXED64)
         e = launch_cluster_mode<MD_ACCUM_FIXED64>(mi, gather, stats, c, grid, stream);

@@ -147,9 +147,10 @@ def test_forces_match_oracle(cuda_lib, name, mode):
 @pytest.mark.parametrize("name", list(SYSTEMS))
 @pytest.mark.parametrize("count", [False, True])
 def test_f32_forces_without_energies_match_oracle(cuda_lib, name, count):
-    """The FP32 force call without energies (the long-row form of the cluster kernel on
-    boxes with >= 3 cells per axis), with and without the pair count, against the oracle;
-    run twice so that nothing depends on what an earlier kernel left in shared memory."""
+    """The FP32 force call without energies, with and without the pair count, against the
+    oracle (at these sizes the one-cluster-pair form runs: too few cells to fill the
+    long-row grid); twice, so that nothing depends on what an earlier kernel left in
+    shared memory."""
     api = cuda_lib
     s, ff, p, ref, alts, nb = ref_for(name)
     for _ in range(2):
@@ -392,6 +393,40 @@ def _largest_reference():
         Fo, cond, _ = oracle.forces_atoms(p, s.q, s.type, s.box, ff, sel)
         _cache["largest"] = (s, sel, Fo, cond, ~_boundary_atoms(p, s.box, s.rc, sel))
     return _cache["largest"]
+
+
+def _lattice92k_reference():
+    """The 92,224-atom lattice and the oracle's forces on every atom, with the boundary-pair
+    alternatives (computed once per test session)."""
+    if "92k" not in _cache:
+        s = W.lattice_box(n=W.APOA1_N)
+        ff = oracle.ForceField.from_system(s)
+        p = s.pos.astype(np.float64)
+        ref = oracle.forces_cells(p, s.q, s.type, s.box, ff)
+        alts, nb = boundary_alternatives(p, s, ff, ref.F)
+        _cache["92k"] = (s, ref, alts, nb)
+    return _cache["92k"]
+
+
+@pytest.mark.parametrize("count", [False, True])
+def test_f32_long_rows_92k_whole_system(cuda_lib, count):
+    """The FP32 force call on the 92,224-atom lattice (the long-row form of the cluster
+    kernel: 486 cells fill its grid), every atom against the oracle, with and without
+    the pair count; twice, so that nothing depends on what an earlier kernel left in
+    shared memory."""
+    api = cuda_lib
+    s, ref, alts, nb = _lattice92k_reference()
+    for _ in range(2):
+        eng = api.Engine(s, mode=api.ACCUM_F32, algo=api.ALGO_CLUSTER)
+        eng.build_cells()
+        eng.compute_forces(energy=False, count=count)
+        torch.cuda.synchronize()
+        assert int(eng.status.item()) == 0
+        F = api.forces_to_f64(eng.forces, api.ACCUM_F32).cpu().numpy()
+        err = force_errors(F, ref.F, ref.cond, alts)
+        assert err["max_norm"] <= TOL_F32, (count, err, nb)
+        if count:
+            assert abs(int(eng.pair_count.item()) - ref.npairs) <= nb
 
 
 @pytest.mark.parametrize("mode", ["f32", "fixed64"])
