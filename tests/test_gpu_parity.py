@@ -382,17 +382,18 @@ def _boundary_atoms(p, box, rc, sel):
     return out
 
 
-def _largest_reference():
-    """The 1,475,584-atom lattice, 2,048 sampled atoms, their oracle forces and which of
-    them have no boundary pair (computed once per test session)."""
-    if "largest" not in _cache:
-        s = W.lattice_box(n=W.APOA1_N * 16)
+def _sampled_reference(n):
+    """The lattice of n atoms, 2,048 sampled atoms, their oracle forces and which of them
+    have no boundary pair (computed once per test session)."""
+    key = ("sampled", n)
+    if key not in _cache:
+        s = W.lattice_box(n=n)
         sel = np.random.default_rng(3).choice(s.n, size=2048, replace=False).astype(np.int32)
         ff = oracle.ForceField.from_system(s)
         p = s.pos.astype(np.float64)
         Fo, cond, _ = oracle.forces_atoms(p, s.q, s.type, s.box, ff, sel)
-        _cache["largest"] = (s, sel, Fo, cond, ~_boundary_atoms(p, s.box, s.rc, sel))
-    return _cache["largest"]
+        _cache[key] = (s, sel, Fo, cond, ~_boundary_atoms(p, s.box, s.rc, sel))
+    return _cache[key]
 
 
 def _lattice92k_reference():
@@ -429,13 +430,15 @@ def test_f32_long_rows_92k_whole_system(cuda_lib, count):
             assert abs(int(eng.pair_count.item()) - ref.npairs) <= nb
 
 
+@pytest.mark.parametrize("n", [W.APOA1_N // 4, W.APOA1_N * 4, W.APOA1_N * 16])
 @pytest.mark.parametrize("mode", ["f32", "fixed64"])
-def test_largest_sweep_size_sampled(cuda_lib, mode):
-    """1,475,584 atoms, the largest point of the size sweep, in the launch the force
-    call makes: 2,048 sampled atoms against the oracle; in FIXED64 Newton's third law
-    holds exactly over the whole system."""
+def test_sweep_sizes_sampled(cuda_lib, n, mode):
+    """The other points of the size sweep (23,056, 368,896 and 1,475,584 atoms; the first
+    runs the one-cluster-pair form, the others the long-row form in FP32), in the launch
+    the force call makes: 2,048 sampled atoms against the oracle; in FIXED64 Newton's third
+    law holds exactly over the whole system."""
     api = cuda_lib
-    s, sel, Fo, cond, use = _largest_reference()
+    s, sel, Fo, cond, use = _sampled_reference(n)
     m = api.ACCUM_F32 if mode == "f32" else api.ACCUM_FIXED64
     eng = run_forces(api, s, m, algo=0, energy=False)
     assert int(eng.status.item()) == 0
