@@ -1422,11 +1422,13 @@ cudaError_t launch_cluster(const ForceArgs &a, const WsLayout &ws, char *wsp, Pa
     if (gather && !a.presorted) return cudaErrorInvalidValue;
     dim3 grid(a.box.ncell, per_cell);
     const int stats = a.energy_virial_out ? kStatsEnergy : (a.pair_count_out ? kStatsCount : kStatsNone);
-    // the long-row form where its grid (4 CTAs a cell) fills at least two waves of 4 CTAs
-    // per SM; smaller grids leave SMs idle, and the one-cluster-pair grid (14 a cell) is
-    // faster there
+    // the long-row form where its grid (4 CTAs a cell) fills at least one wave of 4 CTAs
+    // per SM and the cells hold at most 225 atoms on average (fuller cells more often
+    // exceed its 256-atom tiles); elsewhere the one-cluster-pair grid (14 CTAs a cell) was
+    // measured faster
     if (a.mode == MD_ACCUM_F32 && !mi && !gather && stats != kStatsEnergy && c.cbox &&
-        (long long)a.box.ncell * kRowGroups >= 8LL * device_sms())
+        (long long)a.box.ncell * kRowGroups >= 4LL * device_sms() &&
+        (long long)a.n <= 225LL * a.box.ncell)
         e = launch_cluster_rows(stats, c, a.box.ncell, stream);
     else if (a.mode == MD_ACCUM_FIXED64)
         e = launch_cluster_mode<MD_ACCUM_FIXED64>(mi, gather, stats, c, grid, stream);
