@@ -339,8 +339,10 @@ k_sort_cluster(int *__restrict__ cell_start, const int *__restrict__ perm_tmp,
                int32_t *__restrict__ type_sorted, const int *__restrict__ run_flag,
                float4 *__restrict__ x_ref, float4 *__restrict__ clu_box)
 {
-    __shared__ unsigned long long s_key[kClusterSortMax];  // by arrival
-    __shared__ unsigned long long s_bkt[kClusterSortMax];  // grouped by column
+    // keys by arrival, then grouped by column; after the ranking, the cell's positions in
+    // cluster order (for the cluster boxes)
+    __shared__ __align__(16) unsigned long long s_kb[2 * kClusterSortMax];
+    unsigned long long *s_key = s_kb, *s_bkt = s_kb + kClusterSortMax;
     __shared__ int s_col[kClusterCols + 1];                // counts, then column starts
     __shared__ int s_fill[kClusterCols];
     __shared__ int s_wcnt[kSortThreads / 32];
@@ -386,7 +388,7 @@ k_sort_cluster(int *__restrict__ cell_start, const int *__restrict__ perm_tmp,
     auto boxes = [&]() {
         if (!clu_box) return;
         __syncthreads();
-        write_cluster_boxes<kSortThreads>(pos_q_sorted, s0, m, clu_box, n);
+        write_cluster_boxes<kSortThreads>(pos_q_sorted + s0, s0, m, clu_box, n);
     };
     const int *mem = bin_cap ? bins + (size_t)cg * bin_cap : perm_tmp + s0;
     if (bin_cap && m > bin_cap) {
@@ -488,21 +490,38 @@ k_sort_cluster(int *__restrict__ cell_start, const int *__restrict__ perm_tmp,
         s_bkt[s_col[col] + atomicAdd(&s_fill[col], 1)] = key;
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < m; t += kSortThreads) {
-        const unsigned long long key = s_key[t];
-        const int col = (int)(key >> 54);
-        const int b0 = s_col[col], b1 = s_col[col + 1];
-        int rank = 0;
-        for (int u = b0; u < b1; ++u) rank += s_bkt[u] < key;
-        // what place() writes, from the copies staged above
-        const int slot = s0 + b0 + rank;
-        const int e = (int)(key & ((1ull << 30) - 1));
-        perm[slot] = e;
-        pos_q_sorted[slot] = s_pos[t];
-        type_sorted[slot] = s_typ[t];
-        if (x_ref) x_ref[e] = s_pos[t];
+    constexpr int kPer = kClusterSortMax / kSortThreads;  // members per thread at most
+    int rk[kPer];
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+        const int t = threadIdx.x + i * kSortThreads;
+        rk[i] = -1;
+        if (t < m) {
+            const unsigned long long key = s_key[t];
+            const int col = (int)(key >> 54);
+            const int b0 = s_col[col], b1 = s_col[col + 1];
+            int rank = 0;
+            for (int u = b0; u < b1; ++u) rank += s_bkt[u] < key;
+            // what place() writes, from the copies staged above
+            const int slot = s0 + b0 + rank;
+            const int e = (int)(key & ((1ull << 30) - 1));
+            perm[slot] = e;
+            pos_q_sorted[slot] = s_pos[t];
+            type_sorted[slot] = s_typ[t];
+            if (x_ref) x_ref[e] = s_pos[t];
+            rk[i] = b0 + rank;
+        }
     }
-    boxes();
+    if (clu_box) {
+        // the cluster boxes from the positions placed in shared memory in cluster order
+        float4 *s_ord = reinterpret_cast<float4 *>(s_kb);
+        __syncthreads();  // every rank formed: the keys are no longer read
+#pragma unroll
+        for (int i = 0; i < kPer; ++i)
+            if (rk[i] >= 0) s_ord[rk[i]] = s_pos[threadIdx.x + i * kSortThreads];
+        __syncthreads();
+        write_cluster_boxes<kSortThreads>(s_ord, s0, m, clu_box, n);
+    }
 }
 
 }  // namespace

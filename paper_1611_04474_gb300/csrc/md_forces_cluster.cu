@@ -92,7 +92,7 @@ k_cluster_order(const int32_t *__restrict__ cell_start, const float4 *__restrict
             cty[b + t] = ty[b + t];
         }
         __syncthreads();
-        write_cluster_boxes<kOrderThreads>(cpq, b, m, cbox, n);
+        write_cluster_boxes<kOrderThreads>(cpq + b, b, m, cbox, n);
         return;
     }
     const int nx = box.dims[0], ny = box.dims[1];
@@ -148,7 +148,7 @@ k_cluster_order(const int32_t *__restrict__ cell_start, const float4 *__restrict
         cty[b + rank] = ty[b + t];
     }
     __syncthreads();
-    write_cluster_boxes<kOrderThreads>(cpq, b, m, cbox, n);
+    write_cluster_boxes<kOrderThreads>(cpq + b, b, m, cbox, n);
 }
 
 // Packed pairs of FP32 values (element 0 in the low half).

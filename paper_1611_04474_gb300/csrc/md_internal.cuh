@@ -363,18 +363,19 @@ __device__ __forceinline__ T warp_sum(T v)
     return v;
 }
 
-// Bounding boxes of the clusters (8 consecutive slots) of one cell whose m atoms start at
-// slot s0 of p, in the cell's final order: lo at box[first slot], hi at box[n + first
-// slot]; the last cluster's empty slots are left out.  The cell's atoms must have been
-// written before (the caller synchronises its block first).
+// Bounding boxes of the clusters (8 consecutive slots) of one cell of m atoms in its final
+// order, p pointing at its first atom (which is slot s0): lo at box[first slot], hi at
+// box[n + first slot]; the last cluster's empty slots are left out.  The cell's atoms
+// must have been written before (the caller synchronises its block first).
 template <int NT>
 __device__ __forceinline__ void write_cluster_boxes(const float4 *p, int s0, int m, float4 *box, int n)
 {
     for (int k = threadIdx.x; 8 * k < m; k += NT) {
         const int b = s0 + 8 * k, e = min(m - 8 * k, 8);
-        float4 lo = p[b], hi = lo;
+        const float4 *c = p + 8 * k;
+        float4 lo = c[0], hi = lo;
         for (int t = 1; t < e; ++t) {
-            const float4 q = p[b + t];
+            const float4 q = c[t];
             lo.x = fminf(lo.x, q.x); hi.x = fmaxf(hi.x, q.x);
             lo.y = fminf(lo.y, q.y); hi.y = fmaxf(hi.y, q.y);
             lo.z = fminf(lo.z, q.z); hi.z = fmaxf(hi.z, q.z);
