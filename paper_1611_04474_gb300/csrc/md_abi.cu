@@ -107,12 +107,19 @@ int bin_capacity(int n, int ncell)
     return (int)(cap < (1LL << 30) ? cap : (1LL << 30));
 }
 
-WsLayout ws_layout(int n, int ncell, bool bins, bool verlet)
+// Whether a cell grid has an axis of 2 cells (or fewer): per-pair minimum image.
+static bool split_dims(const int32_t *d)
+{
+    return d[0] < 3 || d[1] < 3 || d[2] < 3;
+}
+
+WsLayout ws_layout(int n, int ncell, bool bins, bool verlet, bool split)
 {
     WsLayout w;
     size_t nn = (size_t)(n > 0 ? n : 1);
     size_t nc = (size_t)(ncell > 0 ? ncell : 1);
-    int slots = 27 * ncell;  // one partial per CTA of a cell-pair kernel at most
+    // one partial per CTA of a cell-pair kernel at most
+    int slots = 27 * (split ? kMiSplit : 1) * ncell;
     int kin = (int)((nn + 255) / 256);
     if (slots < kin) slots = kin;
     if (slots < 2048) slots = 2048;
@@ -172,7 +179,7 @@ static int batch_layout(int32_t nsys, const md_system_desc *systems, BatchLayout
     bl->cell_sys = off;  off = align_up(off + sizeof(int) * (size_t)ncell);
     bl->cell_list = off; off = align_up(off + sizeof(int) * (size_t)ncell);
     bl->atom_sys = off;  off = align_up(off + sizeof(int) * (size_t)(n > 0 ? n : 1));
-    bl->run = ws_layout((int)n, (int)ncell, false);
+    bl->run = ws_layout((int)n, (int)ncell, false, false, ncell_mi > 0);
     bl->run_base = off;
     bl->total = off + bl->run.total;
     return MD_OK;
@@ -209,7 +216,7 @@ size_t md_workspace_bytes(int32_t n, const int32_t *dims)
 {
     int ncell = 0;
     if (n < 0 || n > kMaxAtoms || check_dims(dims, &ncell) != MD_OK) return 0;
-    return ws_layout(n, ncell).total + kAlign;
+    return ws_layout(n, ncell, true, false, split_dims(dims)).total + kAlign;
 }
 
 int md_build_cells(const float *pos_q, const int32_t *type, int32_t n, const double *box_L,
@@ -225,7 +232,7 @@ int md_build_cells(const float *pos_q, const int32_t *type, int32_t n, const dou
     if (!cell_start) return MD_ERR_INVALID_ARG;
     if (n > 0 && (!pos_q || !type || !perm || !pos_q_sorted || !type_sorted)) return MD_ERR_INVALID_ARG;
     if ((pos_q && !aligned16(pos_q)) || (pos_q_sorted && !aligned16(pos_q_sorted))) return MD_ERR_INVALID_ARG;
-    WsLayout ws = ws_layout(n, ncell);
+    WsLayout ws = ws_layout(n, ncell, true, false, split_dims(dims));
     char *wsp = ws_base(workspace, ws_bytes, ws);
     if (!wsp) return MD_ERR_WORKSPACE;
     BoxF box = make_box(box_L, dims);
@@ -262,7 +269,7 @@ int md_nonbonded_forces_algo(const int32_t *cell_start, const int32_t *perm,
     if (!cell_start) return MD_ERR_INVALID_ARG;
     if (n > 0 && (!perm || !pos_q_sorted || !type_sorted || !forces_out)) return MD_ERR_INVALID_ARG;
     if (pos_q_sorted && !aligned16(pos_q_sorted)) return MD_ERR_INVALID_ARG;
-    WsLayout ws = ws_layout(n, ncell);
+    WsLayout ws = ws_layout(n, ncell, true, false, split_dims(dims));
     char *wsp = ws_base(workspace, ws_bytes, ws);
     if (!wsp) return MD_ERR_WORKSPACE;
     ForceArgs a;
@@ -315,7 +322,7 @@ int md_step(double *pos, double *vel, void *forces, int32_t forces_valid, const 
     if ((e = compute_dims(box_L, ff->rc, dims))) return e;
     if (n > 0 && (!pos || !vel || !forces || !inv_mass || !q || !type)) return MD_ERR_INVALID_ARG;
     int ncell = dims[0] * dims[1] * dims[2];
-    WsLayout ws = ws_layout(n, ncell);
+    WsLayout ws = ws_layout(n, ncell, true, false, split_dims(dims));
     char *wsp = ws_base(workspace, ws_bytes, ws);
     if (!wsp) return MD_ERR_WORKSPACE;
     if (n == 0 || (n_steps == 0 && forces_valid)) return MD_OK;
@@ -386,7 +393,7 @@ size_t md_verlet_workspace_bytes(int32_t n, const double *box_L, double rc, doub
     int32_t dims[3];
     if (n < 0 || n > kMaxAtoms || !(skin > 0.0) || !isfinite(skin)) return 0;
     if (compute_dims(box_L, rc + skin, dims) != MD_OK) return 0;
-    return ws_layout(n, dims[0] * dims[1] * dims[2], false, true).total + kAlign;
+    return ws_layout(n, dims[0] * dims[1] * dims[2], false, true, split_dims(dims)).total + kAlign;
 }
 
 int md_step_verlet(double *pos, double *vel, void *forces, int32_t forces_valid,
@@ -408,7 +415,7 @@ int md_step_verlet(double *pos, double *vel, void *forces, int32_t forces_valid,
     if ((e = compute_dims(box_L, ff->rc + skin, dims))) return e;  // the Verlet grid
     if (n > 0 && (!pos || !vel || !forces || !inv_mass || !q || !type)) return MD_ERR_INVALID_ARG;
     const int ncell = dims[0] * dims[1] * dims[2];
-    WsLayout ws = ws_layout(n, ncell, false, true);
+    WsLayout ws = ws_layout(n, ncell, false, true, split_dims(dims));
     char *wsp = ws_base(workspace, ws_bytes, ws);
     if (!wsp) return MD_ERR_WORKSPACE;
     if (n == 0 || (n_steps == 0 && forces_valid)) return MD_OK;

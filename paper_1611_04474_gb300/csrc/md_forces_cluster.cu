@@ -525,19 +525,21 @@ __device__ __forceinline__ bool crossed_face(const float4 &p, const float *centr
            fabsf(p.z - centre[2]) > half_L[2];
 }
 
-// One cell pair: cell cx of the launch (of gx) with stencil entry cy.
+// One cell pair: cell cx of the launch (of gx) with stencil entry cy (of gy), or the
+// share z of zs of its home clusters (rows z, z + zs, ...: boxes with an axis of 2 cells
+// split each cell pair over kMiSplit CTAs, whose few cell pairs are long).
 template <int MODE, int STATS, bool BATCHED, bool MI, bool GATHER = false>
 __device__ __forceinline__ void cluster_item(CluSmem<MODE> &sm, float2 *s_ab, const CluArgs &a,
                                              const BatchArgs &bt,
                                              unsigned long long *sys_pair_count, int cx, int cy,
-                                             int gx)
+                                             int gx, int z = 0, int zs = 1, int gy = 1)
 {
     using Acc = typename AccT<MODE>::T;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float e_lj = 0.f, e_c = 0.f, vir = 0.f;
     unsigned cnt = 0;
-    Partial *mine = a.partials + (size_t)cy * gx;
+    Partial *mine = a.partials + ((size_t)z * gy + cy) * gx;
 
     // the system this CTA works on: the only one, or the one its cell belongs to
     PairGeom g;
@@ -705,7 +707,10 @@ __device__ __forceinline__ void cluster_item(CluSmem<MODE> &sm, float2 *s_ab, co
             // home clusters handed out one at a time, so that warps finish together;
             // MD_ACCUM_FIXED_TILE deals them in a fixed order (warp w takes w, w + kCW, ...)
             // so that every warp-private partial sum is formed in the same order each run
-            for (int ic = warp; ic < nic;) {
+            // (this CTA's rows: home clusters z, z + zs, ...)
+            const int nrow = nic > z ? (nic - z + zs - 1) / zs : 0;
+            for (int r = warp; r < nrow;) {
+                const int ic = r * zs + z;
                 if (diag)
                     cluster_row<MODE, STATS, true, false, MI, GATHER>(sm, s_ab, k, ic, njc, mh, warp, lane, e_lj, e_c, vir, cnt);
                 else if (!MI && shift)
@@ -713,11 +718,11 @@ __device__ __forceinline__ void cluster_item(CluSmem<MODE> &sm, float2 *s_ab, co
                 else
                     cluster_row<MODE, STATS, false, false, MI, GATHER>(sm, s_ab, k, ic, njc, mh, warp, lane, e_lj, e_c, vir, cnt);
                 if (MODE == MD_ACCUM_FIXED_TILE) {
-                    ic += kCW;
+                    r += kCW;
                 } else {
                     int nx = 0;
                     if (lane == 0) nx = atomicAdd(&sm.next, 1);
-                    ic = __shfl_sync(0xffffffffu, nx, 0);
+                    r = __shfl_sync(0xffffffffu, nx, 0);
                 }
             }
             __syncthreads();
@@ -776,7 +781,7 @@ constexpr int clu_min_blocks()
 template <int MODE, int STATS, bool BATCHED, bool MI, bool PERSIST, bool GATHER = false>
 __global__ void __launch_bounds__(kCT, (clu_min_blocks<MODE, STATS, PERSIST>()))
 k_cluster(CluArgs a, BatchArgs bt, unsigned long long *sys_pair_count, int *work, int ncells,
-          int per_cell)
+          int per_cell, int zsplit)
 {
     __shared__ __align__(16) CluSmem<MODE> sm;
     extern __shared__ __align__(16) unsigned char s_dyn[];
@@ -785,19 +790,22 @@ k_cluster(CluArgs a, BatchArgs bt, unsigned long long *sys_pair_count, int *work
     pdl_trigger();
     if (!PERSIST) {
         cluster_item<MODE, STATS, BATCHED, MI, GATHER>(sm, s_ab, a, bt, sys_pair_count, blockIdx.x,
-                                                       blockIdx.y, gridDim.x);
+                                                       blockIdx.y, gridDim.x, blockIdx.z, gridDim.z,
+                                                       gridDim.y);
         return;
     }
     __shared__ int s_item;
-    const int nitems = ncells * per_cell;
+    const int nitems = ncells * per_cell * zsplit;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(work, 1);
         __syncthreads();
         const int item = s_item;
         __syncthreads();
         if (item >= nitems) break;
-        cluster_item<MODE, STATS, BATCHED, MI>(sm, s_ab, a, bt, sys_pair_count, item % ncells,
-                                               item / ncells, ncells);
+        const int pair = item % (ncells * per_cell);
+        cluster_item<MODE, STATS, BATCHED, MI>(sm, s_ab, a, bt, sys_pair_count, pair % ncells,
+                                               pair / ncells, ncells, item / (ncells * per_cell),
+                                               zsplit, per_cell);
     }
 }
 
@@ -1299,8 +1307,9 @@ k_finalize_clu(const void *__restrict__ accum, const int32_t *__restrict__ corde
     }
 }
 
-// grid: cells x stencil entries.  PERSIST: the same items from about one wave of CTAs
-// (blocks per SM at this launch's shared memory x SMs), taking items from `work`.
+// grid: cells x stencil entries x shares of a cell pair (kMiSplit for boxes with an axis
+// of 2 cells, else 1).  PERSIST: the same items from about one wave of CTAs (blocks per
+// SM at this launch's shared memory x SMs), taking items from `work`.
 template <int MODE, int STATS, bool BATCHED = false, bool MI = false, bool PERSIST = false,
           bool GATHER = false>
 cudaError_t launch_cluster_t(const CluArgs &c, dim3 grid, cudaStream_t stream,
@@ -1321,11 +1330,11 @@ cudaError_t launch_cluster_t(const CluArgs &c, dim3 grid, cudaStream_t stream,
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cluster<MODE, STATS, BATCHED, MI, PERSIST, GATHER>,
                                                       kCT, dyn);
         const long long wave = (long long)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
-        const long long items = (long long)grid.x * grid.y;
+        const long long items = (long long)grid.x * grid.y * grid.z;
         g = dim3((unsigned)(items < wave ? items : wave), 1);
     }
     return launch_pdl(k_cluster<MODE, STATS, BATCHED, MI, PERSIST, GATHER>, g, dim3(kCT), dyn, stream, c, b,
-                      sys_pair_count, work, (int)grid.x, (int)grid.y);
+                      sys_pair_count, work, (int)grid.x, (int)grid.y, (int)grid.z);
 }
 
 template <int MODE, bool MI, bool GATHER = false>
@@ -1420,7 +1429,7 @@ cudaError_t launch_cluster(const ForceArgs &a, const WsLayout &ws, char *wsp, Pa
     c.cbox = a.presorted ? a.clu_box : cbox;
     const bool gather = a.gather_pq != nullptr;
     if (gather && !a.presorted) return cudaErrorInvalidValue;
-    dim3 grid(a.box.ncell, per_cell);
+    dim3 grid(a.box.ncell, per_cell, mi ? kMiSplit : 1);
     const int stats = a.energy_virial_out ? kStatsEnergy : (a.pair_count_out ? kStatsCount : kStatsNone);
     // the long-row form where its grid (4 CTAs a cell) fills at least one wave of 4 CTAs
     // per SM and the cells hold at most 225 atoms on average (fuller cells more often
@@ -1436,7 +1445,7 @@ cudaError_t launch_cluster(const ForceArgs &a, const WsLayout &ws, char *wsp, Pa
         e = launch_cluster_mode<MD_ACCUM_FIXED_TILE>(mi, gather, stats, c, grid, stream);
     else
         e = launch_cluster_mode<MD_ACCUM_F32>(mi, gather, stats, c, grid, stream);
-    *nblocks_out = a.box.ncell * per_cell;
+    *nblocks_out = a.box.ncell * per_cell * (int)grid.z;
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return launch_finalize_cluster(a, accum, ws, wsp, a.n, stream);
@@ -1470,7 +1479,7 @@ cudaError_t launch_cluster_batched(int mode, bool mi, const BatchArgs &b, const 
     c.n = b.n;
     c.partials = partials;
     c.status = status;
-    dim3 grid(ncells, mi ? 27 : 14);
+    dim3 grid(ncells, mi ? 27 : 14, mi ? kMiSplit : 1);
     unsigned long long *cnt = sys_pair_count;
     int *w = persist_work;
     const int sel = (mode == MD_ACCUM_FIXED64 ? 4 : mode == MD_ACCUM_FIXED_TILE ? 8 : 0) + (mi ? 2 : 0) + (w ? 1 : 0);

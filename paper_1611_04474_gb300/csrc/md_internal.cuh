@@ -82,10 +82,16 @@ struct WsLayout {
     int bin_cap;        // 0: no bins (the step scatters through perm_tmp)
 };
 
+// CTAs that share one cell pair of the cluster-pair kernel in boxes with an axis of 2
+// cells (their few cell pairs are long), each taking every kMiSplit-th home cluster.
+constexpr int kMiSplit = 4;
+
 // Members per cell that the MD step's bins hold: twice the mean occupancy plus 64,
 // rounded up to 32.  A cell with more members is gathered by a scan of the cell ids.
 int bin_capacity(int n, int ncell);
-WsLayout ws_layout(int n, int ncell, bool bins = true, bool verlet = false);
+// split: the box has an axis of 2 cells (its cluster-pair CTAs are split kMiSplit ways,
+// each with a partial); the default reserves for that case
+WsLayout ws_layout(int n, int ncell, bool bins = true, bool verlet = false, bool split = true);
 
 // Device state of the Verlet step (md_step_verlet), in its workspace.
 struct VerletFlags {
