@@ -1429,7 +1429,10 @@ cudaError_t launch_cluster(const ForceArgs &a, const WsLayout &ws, char *wsp, Pa
     c.cbox = a.presorted ? a.clu_box : cbox;
     const bool gather = a.gather_pq != nullptr;
     if (gather && !a.presorted) return cudaErrorInvalidValue;
-    dim3 grid(a.box.ncell, per_cell, mi ? kMiSplit : 1);
+    // a system alone with an axis of 2 cells: its few long cell pairs split over kMiSplit
+    // CTAs (not in MD_ACCUM_FIXED_TILE, whose rounding points would move, and whose single
+    // and batched results are the same bits; batches fill the GPU without it)
+    dim3 grid(a.box.ncell, per_cell, mi && a.mode != MD_ACCUM_FIXED_TILE ? kMiSplit : 1);
     const int stats = a.energy_virial_out ? kStatsEnergy : (a.pair_count_out ? kStatsCount : kStatsNone);
     // the long-row form where its grid (4 CTAs a cell) fills at least one wave of 4 CTAs
     // per SM and the cells hold at most 225 atoms on average (fuller cells more often
@@ -1479,7 +1482,7 @@ cudaError_t launch_cluster_batched(int mode, bool mi, const BatchArgs &b, const 
     c.n = b.n;
     c.partials = partials;
     c.status = status;
-    dim3 grid(ncells, mi ? 27 : 14, mi ? kMiSplit : 1);
+    dim3 grid(ncells, mi ? 27 : 14);
     unsigned long long *cnt = sys_pair_count;
     int *w = persist_work;
     const int sel = (mode == MD_ACCUM_FIXED64 ? 4 : mode == MD_ACCUM_FIXED_TILE ? 8 : 0) + (mi ? 2 : 0) + (w ? 1 : 0);
