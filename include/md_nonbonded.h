@@ -84,7 +84,11 @@ extern "C" {
 #define MD_ALGO_HALF_SHELL 2 /* each cell pair once, reactions by Newton's third law */
 #define MD_ALGO_CLUSTER 3    /* the half shell filtered by clusters of 8 atoms, every pair of
                                 a cluster pair in range evaluated (per-pair minimum image in
-                                boxes with an axis of 2 cells) */
+                                boxes with an axis of 2 cells).  MD_ACCUM_F32 without
+                                energies, on grids large enough to fill the GPU: each home
+                                cluster against all its in-range neighbour clusters of a
+                                group of cells at once; otherwise one cluster pair per warp
+                                step.  The two give the same forces up to FP32 rounding. */
 
 /* Force-field constants of Eq. 1-2.  Host struct; AB is a DEVICE pointer to
  * float[ntypes][ntypes][2] holding (A_ij, B_ij) of Eq. 1 (symmetric in i,j). */
@@ -181,8 +185,8 @@ int md_build_cells_noalloc(const float *pos_q, const int32_t *type, int32_t n,
  *                 (F = f r); summed per block and then in a fixed order
  *   pair_count_out     device uint64[1] or NULL: unique pairs with r^2 < rc^2
  * Forces and counts of modes FIXED64, F64 and FIXED_TILE are reproducible bit for bit;
- * F32 adds partial sums (per home cluster and per tile) with floating-point atomics and
- * may differ in the last bits between runs.  MD_ERR_INVALID_ARG for MD_ACCUM_FIXED_TILE
+ * F32 adds partial sums (per home cluster and row or tile, per neighbour atom and step or
+ * tile) with floating-point atomics and may differ in the last bits between runs.  MD_ERR_INVALID_ARG for MD_ACCUM_FIXED_TILE
  * with MD_ALGO_FULL_SHELL or MD_ALGO_HALF_SHELL.
  */
 int md_nonbonded_forces(const int32_t *cell_start, const int32_t *perm, const float *pos_q_sorted,
