@@ -838,6 +838,7 @@ constexpr int kRowDummy = kRowClu;     // a cluster of padding atoms, for partia
 constexpr int kRowSlots = (kRowClu + 1) * kCS;
 constexpr int kRowList = kRowClu + 8;  // diagonal entry + padding for the last step and the prefetch
 constexpr int kRowABStride = 5;        // float4 per neighbour type in a row's LJ table
+constexpr int kRedRow = 25;            // floats per lane in the row-end reduction (24 + 1 pad)
 
 // Half-shell entries (0: the cell itself; j: forward neighbour j) of the four groups,
 // heaviest group first (about 840, 760, 760 and 510 cluster pairs in range at the
@@ -862,6 +863,7 @@ struct RowSmem {
     int gbeg[kRowCells], gm[kRowCells];   // cell's first slot in the sorted arrays, atoms
     int ccell[kRowCells + 1];             // first cell of each class
     float chs[kRowCells][3], clo[kRowCells][3];  // hs and lo of each class
+    float red[kRW][32 * kRedRow];         // each warp's home partials at the end of a row
 };
 
 // Four neighbour clusters against the row's home cluster: this lane's neighbour atom ja
@@ -1022,37 +1024,39 @@ __device__ __forceinline__ void row_run(RowSmem &sm, const float2 *s_ab, float4 
             row_steps<STATS, false>(sm, static_cast<float4 *>(a.accum), rab, lst, len, diag, lane, HX, HY, HZ, KQ, FX, FY, FZ, LX, LY, LZ, a.rc2, cnt);
         __syncwarp();
     }
-    // the 24 home sums (atom 2p and 2p + 1, x y z) over the warp: a reduce-scatter over the
-    // five lane bits, after which lane l < 24 holds sum l (atom l / 3, component l % 3)
-    float w[32];
+    // the 24 home sums (value 3 k + d: atom k, component d) over the warp: each lane
+    // writes its row of partials to the warp's shared array and lane l < 24 sums column l
+    float *red = sm.red[threadIdx.x >> 5];
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
-        f2_split(FX[p], w[6 * p + 0], w[6 * p + 3]);
-        f2_split(FY[p], w[6 * p + 1], w[6 * p + 4]);
-        f2_split(FZ[p], w[6 * p + 2], w[6 * p + 5]);
+        float a0, a1;
+        f2_split(FX[p], a0, a1);
+        red[lane * kRedRow + 6 * p + 0] = a0;
+        red[lane * kRedRow + 6 * p + 3] = a1;
+        f2_split(FY[p], a0, a1);
+        red[lane * kRedRow + 6 * p + 1] = a0;
+        red[lane * kRedRow + 6 * p + 4] = a1;
+        f2_split(FZ[p], a0, a1);
+        red[lane * kRedRow + 6 * p + 2] = a0;
+        red[lane * kRedRow + 6 * p + 5] = a1;
     }
-#pragma unroll
-    for (int q = 24; q < 32; ++q) w[q] = 0.0f;
-#pragma unroll
-    for (int half = 16; half >= 1; half >>= 1) {
-        const bool up = (lane & half) != 0;  // keep the upper half of the current values
-#pragma unroll
-        for (int q = 0; q < half; ++q) {
-            const float send = up ? w[q] : w[q + half];
-            const float keep = up ? w[q + half] : w[q];
-            w[q] = keep + __shfl_xor_sync(0xffffffffu, send, half);
-        }
-    }
-    // lane l's sum is value l when the bits of l select the kept halves: bit 4 of l chose
-    // the upper 16 values first, and so on down, so value index = l
+    __syncwarp();
     if (lane < 24) {
+        float v[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int r = 0; r < 32; r += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] += red[(r + u) * kRedRow + lane];
+        }
         const int ia = ic * kCS + lane / 3;
         if (ia < mh)
-            atomicAdd(static_cast<float *>(a.accum) + 4 * (size_t)(hb + ia) + lane % 3, w[0]);
+            atomicAdd(static_cast<float *>(a.accum) + 4 * (size_t)(hb + ia) + lane % 3,
+                      (v[0] + v[1]) + (v[2] + v[3]));
     }
+    __syncwarp();
 }
 
-// One cell of a CTA's group (each thread forms them all itself, in registers).
+// One cell of a CTA's group (warp 0 forms and sorts them; the CTA reads them back).
 struct RowRec {
     int key, code, beg, cnt, self;  // sort key: the cell itself, then no wrap, then by code
     float hs[3], ns[3], lo[3];
@@ -1076,45 +1080,59 @@ k_cluster_rows(CluArgs a, int ncells)
     pdl_trigger();
     const int cell = blockIdx.x, grp = blockIdx.y;
     const int hb = a.cell_start[cell], mh = a.cell_start[cell + 1] - hb;
-    // the group's cells, sorted into classes of equal wrap code (the cell itself first)
+    // the group's cells, sorted into classes of equal wrap code (the cell itself first),
+    // formed by warp 0 and shared
+    __shared__ RowRec s_rec[kRowCells];
+    __shared__ int s_ne;
     RowRec r[kRowCells];
     int ne = 0;
+    if (threadIdx.x < 32) {
 #pragma unroll
-    for (int k = 0; k < kRowCells; ++k) {
-        const int e = kRowGroup[grp][k];
-        r[k].key = 1 << 20;
-        r[k].code = -1;
-        r[k].beg = r[k].cnt = r[k].self = 0;
+        for (int k = 0; k < kRowCells; ++k) {
+            const int e = kRowGroup[grp][k];
+            r[k].key = 1 << 20;
+            r[k].code = -1;
+            r[k].beg = r[k].cnt = r[k].self = 0;
 #pragma unroll
-        for (int d = 0; d < 3; ++d) r[k].hs[d] = r[k].ns[d] = r[k].lo[d] = 0.0f;
-        if (e >= 0) {
-            PairGeom q;
-            const int code = forward_pair(a.box, cell, e, q);
-            r[k].code = code;
-            r[k].self = q.self;
-            r[k].key = q.self ? -2 : (code == 13 ? -1 : code);
-            r[k].beg = a.cell_start[q.nbr];
-            r[k].cnt = a.cell_start[q.nbr + 1] - r[k].beg;
+            for (int d = 0; d < 3; ++d) r[k].hs[d] = r[k].ns[d] = r[k].lo[d] = 0.0f;
+            if (e >= 0) {
+                PairGeom q;
+                const int code = forward_pair(a.box, cell, e, q);
+                r[k].code = code;
+                r[k].self = q.self;
+                r[k].key = q.self ? -2 : (code == 13 ? -1 : code);
+                r[k].beg = a.cell_start[q.nbr];
+                r[k].cnt = a.cell_start[q.nbr + 1] - r[k].beg;
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                r[k].hs[d] = q.hs[d];
-                r[k].ns[d] = q.ns[d];
-                r[k].lo[d] = q.lo[d];
-            }
-            ++ne;
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < kRowCells - 1; ++i) {
-#pragma unroll
-        for (int j = 0; j < kRowCells - 1 - i; ++j) {
-            if (r[j].key > r[j + 1].key) {
-                const RowRec t = r[j];
-                r[j] = r[j + 1];
-                r[j + 1] = t;
+                for (int d = 0; d < 3; ++d) {
+                    r[k].hs[d] = q.hs[d];
+                    r[k].ns[d] = q.ns[d];
+                    r[k].lo[d] = q.lo[d];
+                }
+                ++ne;
             }
         }
+#pragma unroll
+        for (int i = 0; i < kRowCells - 1; ++i) {
+#pragma unroll
+            for (int j = 0; j < kRowCells - 1 - i; ++j) {
+                if (r[j].key > r[j + 1].key) {
+                    const RowRec t = r[j];
+                    r[j] = r[j + 1];
+                    r[j + 1] = t;
+                }
+            }
+        }
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int k = 0; k < kRowCells; ++k) s_rec[k] = r[k];
+            s_ne = ne;
+        }
     }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kRowCells; ++k) r[k] = s_rec[k];
+    ne = s_ne;
     bool fits = mh <= kRowCellAtoms;
 #pragma unroll
     for (int k = 0; k < kRowCells; ++k) fits = fits && r[k].cnt <= kRowCellAtoms;
