@@ -32,7 +32,14 @@
 //
 // Boxes with an axis of 2 cells meet each distinct stencil cell once, with unshifted
 // tiles: the filter takes the gap between the clusters' nearest images and each pair
-// the per-pair minimum image.
+// the per-pair minimum image.  For a system alone (FP32, FIXED64) each of their few,
+// long cell pairs is split over kMiSplit CTAs by home cluster.
+//
+// The above is the one-cluster-pair form (k_cluster), used for the fixed-point modes,
+// energies, the Verlet step, batches and small grids.  FP32 forces on grids that fill the
+// GPU run the long-row form (k_cluster_rows, further below): the same pairs, filter and
+// pair math, but each warp takes one home cluster against all its in-range neighbour
+// clusters of a group of cells, with 8 pairs a lane per step.
 #include <math.h>
 
 #include "md_internal.cuh"
