@@ -49,6 +49,48 @@ def test_fixed_tile_matches_oracle(cuda_lib, name):
         assert net <= 1e-6 * np.abs(F).sum(), (net, np.abs(F).sum())
 
 
+def _crowded():
+    """3 x 3 x 3 cells of 512 atoms each: every cell pair takes two 256-atom home tiles and
+    two neighbour tiles, so each home cluster's sums are rounded once per neighbour tile."""
+    from tests.test_gpu_parity import _custom
+
+    g = np.stack(np.meshgrid(*[np.arange(24)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    rng = np.random.default_rng(11)
+    return _custom(0.25 + 0.5 * g + rng.uniform(-0.03, 0.03, g.shape), (12.0, 12.0, 12.0), rc=4.0)
+
+
+_refs = {}
+
+
+@pytest.mark.parametrize("name", list(SYSTEMS) + ["crowded_512"])
+@pytest.mark.parametrize("count", [False, True])
+def test_fixed_tile_forces_without_energies_match_oracle(cuda_lib, name, count):
+    """Forces alone, with and without the pair count (the force call without energy
+    sums), on regular boxes, a box with a 2-cell axis and crowded cells: against the
+    oracle, the same bits on a second call, Newton's third law to FP32 size."""
+    api = cuda_lib
+    if name not in _refs:
+        s = _crowded() if name == "crowded_512" else SYSTEMS[name]()
+        _refs[name] = (s,) + _oracle_ref(s)
+    s, ff, p, ref, alts, nb = _refs[name]
+    runs = []
+    for _ in range(2):
+        eng = api.Engine(s, mode=api.ACCUM_FIXED_TILE, algo=api.ALGO_CLUSTER)
+        eng.build_cells()
+        eng.compute_forces(energy=False, count=count)
+        torch.cuda.synchronize()
+        assert int(eng.status.item()) == 0
+        runs.append(eng.forces.cpu().numpy().copy())
+        F = api.forces_to_f64(eng.forces, api.ACCUM_FIXED_TILE).cpu().numpy()
+        err = force_errors(F, ref.F, ref.cond, alts)
+        assert err["max_norm"] <= TOL_F32, (name, count, err, nb)
+        if count:
+            assert abs(int(eng.pair_count.item()) - ref.npairs) <= nb
+        net = np.abs(runs[-1].sum(axis=0, dtype=np.int64)).max() / 2.0**32
+        assert net <= 1e-6 * np.abs(F).sum(), (net, np.abs(F).sum())
+    assert np.array_equal(runs[0], runs[1])
+
+
 def test_fixed_tile_reproducible_run_to_run(cuda_lib):
     api = cuda_lib
     s = SYSTEMS["lattice_92224"]()
