@@ -908,11 +908,12 @@ __device__ __forceinline__ void row_step(float4 *accum, const float4 *rab, int g
         const f2 ir = f2_make(rsqrt_hw(r2a), rsqrt_hw(r2b));
         const f2 ir2 = f2_mul(ir, ir);
         const f2 ir6 = f2_mul(f2_mul(ir2, ir2), ir2);
-        const f2 ir8 = f2_mul(ir6, ir2);
-        const f2 lj = f2_mul(ir8, f2_fma(A, ir6, nB));
         const f2 kqq = f2_mul(KQ[p], Q);
+        // F/r = (kqq / r + (A / r^6 - B) / r^6) / r^2: one product fewer than forming
+        // 1/r^8 and kqq / r^2 on their own
+        const f2 u = f2_fma(kqq, ir, f2_mul(ir6, f2_fma(A, ir6, nB)));
         float fa, fb;
-        f2_split(f2_fma(f2_mul(kqq, ir2), ir, lj), fa, fb);
+        f2_split(f2_mul(u, ir2), fa, fb);
         const f2 f = f2_make(oka ? fa : 0.0f, okb ? fb : 0.0f);
         FX[p] = f2_fma(f, dx, FX[p]);
         FY[p] = f2_fma(f, dy, FY[p]);
