@@ -72,7 +72,8 @@ def test_precision_study_92k(cuda_lib):
 
 
 def test_precision_study_relaxed_control_92k(cuda_lib):
-    """The same study from the relaxed start (SURVEY C10's control variant).  The
+    """The same study from the relaxed start (the control variant: 200 capped
+    steepest-descent steps of the oracle before the run).  The
     relaxation lowers the potential energy and the heating, but the small LJ cores still
     let opposite charges close in, so the drift mostly measures the 1 fs step against
     those approaches; what is asserted is that the accumulation mode does not change it:
